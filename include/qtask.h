@@ -1,0 +1,205 @@
+/*
+ * qtask.h -- C ABI of libqtask.so, an incremental state-vector quantum-circuit
+ * simulator for one NVIDIA GB300 (sm_103a).
+ *
+ * Method: qTask (T.-W. Huang, arXiv 2210.01076).  A circuit on n qubits is an
+ * ordered list of levels ("nets", Section III-B); the gates of one level act
+ * on disjoint qubits.  The simulator keeps the 2^n complex amplitudes
+ * (Section II-A; qubit q is bit q of the amplitude index, q_0 least
+ * significant, Listing 1) split into fixed partitions of 2^log2_partition
+ * consecutive amplitudes (the paper's blocks, Section III-C).  Circuit
+ * modifiers (insert/remove/replace a gate, insert/remove a level; Table 2)
+ * only record the edit; qt_update_state then re-simulates only the partitions
+ * downstream of the edits (Sections III-D and III-E), starting from device
+ * checkpoints of the state kept at segment boundaries (the per-net state
+ * vectors of Section III-F).  The result is bit-identical to a full
+ * re-simulation of the edited circuit (qt_update_state with force_full = 1).
+ *
+ * Ownership: the library owns every host and device buffer it allocates; the
+ * caller owns every buffer it passes in (gates are copied, never retained).
+ * Errors: every call returns a qt_status; no C++ exception crosses the ABI.
+ * qt_last_error(c) returns a message for the last failed call on c.
+ * Threading: calls on different circuits may run concurrently; calls on one
+ * circuit must be serialised by the caller.
+ * Device: all GPU work of a circuit runs on one CUDA stream (the library's
+ * own, or the one given to qt_set_stream).  Device memory is allocated on the
+ * first call that needs the GPU (qt_update_state, qt_read_amplitudes*,
+ * qt_norm), not by qt_create, so circuit editing works without a GPU.
+ */
+#ifndef QTASK_H
+#define QTASK_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct qt_circuit qt_circuit;
+
+typedef enum {
+    QT_OK = 0,
+    QT_ERR_ARG = 1,       /* bad argument (null pointer, bad qubit, bad kind, ...) */
+    QT_ERR_CONFLICT = 2,  /* the gate shares a qubit with a gate of its level (Section III-B) */
+    QT_ERR_RANGE = 3,     /* level or amplitude index out of range */
+    QT_ERR_NOT_FOUND = 4, /* no gate with that id in that level */
+    QT_ERR_OOM = 5,       /* device memory (or the mem_limit option) exhausted; nothing changed */
+    QT_ERR_CUDA = 6,      /* a CUDA call failed (including: no GPU present) */
+    QT_ERR_STALE = 7,     /* edits are pending: call qt_update_state first */
+    QT_ERR_TIMEOUT = 8    /* a bounded device wait expired */
+} qt_status;
+
+/* Amplitude storage and arithmetic.
+ *   QT_C128    16 B per amplitude, IEEE binary64 (re, im); FP64 arithmetic.
+ *   QT_C64      8 B per amplitude, binary32 (re, im); FP32 arithmetic.
+ *   QT_C128_DF 16 B per amplitude as float-float pairs (re_hi, re_lo, im_hi,
+ *              im_lo), each real held as an unevaluated sum of two binary32
+ *              values (about 48 significand bits); arithmetic in float-float
+ *              on the FP32 pipes, whose rate on GB300 is ~60x its FP64 rate.
+ * qt_read_amplitudes returns binary64 (re, im) pairs for QT_C128 and
+ * QT_C128_DF, binary32 pairs for QT_C64. */
+typedef enum { QT_C128 = 0, QT_C64 = 1, QT_C128_DF = 2 } qt_dtype;
+
+/* Gate kinds: the paper's standard gates (Table 1) and the composites it
+ * names (CZ, CCX, SWAP; Section III-A), plus U3 and the controlled phase CP.
+ * Matrices (c = cos(t/2), s = sin(t/2), t = theta[0]):
+ *   H = [[1,1],[1,-1]]/sqrt2, X = [[0,1],[1,0]], Y = [[0,-i],[i,0]],
+ *   Z = diag(1,-1), S = diag(1,i), SDG = diag(1,-i), T = diag(1,e^{i pi/4}),
+ *   TDG = diag(1,e^{-i pi/4}), RX = [[c,-is],[-is,c]], RY = [[c,-s],[s,c]],
+ *   RZ = diag(e^{-it/2}, e^{it/2}),
+ *   U3(t,p,l) = [[c, -e^{il}s], [e^{ip}s, e^{i(p+l)}c]]  (p = theta[1], l = theta[2]),
+ *   CNOT = X on target[0] controlled by control[0]; CZ = Z controlled;
+ *   CCX = X controlled by control[0] and control[1];
+ *   CP = diag(1, e^{i theta[0]}) on target[0] controlled by control[0];
+ *   SWAP exchanges target[0] and target[1]. */
+typedef enum {
+    QT_H = 0, QT_X, QT_Y, QT_Z, QT_S, QT_SDG, QT_T, QT_TDG, QT_RX, QT_RY, QT_RZ, QT_U3,
+    QT_CNOT, QT_CZ, QT_SWAP, QT_CCX, QT_CP, QT_NUM_KINDS
+} qt_kind;
+
+/* A gate.  ntarget/ncontrol must match the kind (1/0 for one-qubit gates,
+ * 1/1 for CNOT CZ CP, 2/0 for SWAP, 1/2 for CCX); all qubits distinct and
+ * in [0, n).  Copied in by the call; the caller keeps ownership. */
+typedef struct {
+    int32_t kind;
+    int32_t ntarget;
+    int32_t target[2];
+    int32_t ncontrol;
+    int32_t control[2];
+    double theta[3];
+} qt_gate;
+
+/* Stable gate handle, unique within a circuit and never reused. */
+typedef uint64_t qt_gate_id;
+
+/* What one qt_update_state did.  "Partition-passes" count (partition x
+ * fused pass) units: the incremental work unit of Section III-E. */
+typedef struct {
+    int32_t segments_total;      /* checkpoint segments in the plan */
+    int32_t segments_run;        /* segments that launched work */
+    int32_t passes_total;        /* fused passes in the whole plan */
+    int32_t passes_run;          /* fused passes launched */
+    int32_t launches;            /* kernel launches issued */
+    int32_t gates_total;         /* gates in the circuit */
+    int64_t partition_passes_total;     /* sum over all passes of all partitions */
+    int64_t partition_passes_run;       /* sum over launched passes of partitions processed */
+    double clean_fraction;       /* 1 - run / total partition-passes */
+    uint64_t amp_updates;        /* sum over gates of amplitudes processed (full run: gates x 2^n) */
+    uint64_t hbm_bytes;          /* algorithmic bytes: 2 x bytes/amp x amplitudes, per pass */
+    double host_ms;              /* wall time of the call */
+    double gpu_ms;               /* device time of the call's stream work (CUDA events), -1 if not timed */
+    double pass_kernel_ms;       /* summed device time of the fused-pass kernels (option kernel_timing) or -1 */
+    int32_t pass_kernel_launches;
+    int32_t reserved;
+    uint64_t pass_kernel_bytes;  /* algorithmic bytes of those launches */
+    uint64_t h2d_bytes;          /* host-to-device bytes uploaded (fused ops and worklists) */
+} qt_update_stats;
+
+/* Create an empty circuit (no levels) whose state is |0...0>.
+ * n_qubits in [1, 34]; log2_partition in [0, n_qubits] (partition size
+ * 2^log2_partition amplitudes, the paper's block size B, Section III-C).
+ * Allocates host memory only.  *out receives the handle. */
+qt_status qt_create(int32_t n_qubits, int32_t dtype, int32_t log2_partition, qt_circuit** out);
+
+/* Free the circuit and all its host and device memory.  NULL is allowed. */
+qt_status qt_destroy(qt_circuit* c);
+
+qt_status qt_num_levels(const qt_circuit* c, int32_t* out);
+qt_status qt_num_gates(const qt_circuit* c, int64_t* out);
+
+/* Insert an empty level at position pos in [0, num_levels]; levels at and
+ * after pos move up by one (insert_net, Table 2). */
+qt_status qt_insert_level(qt_circuit* c, int32_t pos);
+
+/* Remove level pos and all its gates (remove_net, Table 2). */
+qt_status qt_remove_level(qt_circuit* c, int32_t pos);
+
+/* Add a gate to level `level` (insert_gate, Table 2).  QT_ERR_CONFLICT if it
+ * shares a qubit with a gate already in the level; the circuit is then
+ * unchanged (Section III-B).  *out receives the new gate's id. */
+qt_status qt_insert_gate(qt_circuit* c, int32_t level, const qt_gate* g, qt_gate_id* out);
+
+/* Remove gate `id` from level `level` (remove_gate, Table 2). */
+qt_status qt_remove_gate(qt_circuit* c, int32_t level, qt_gate_id id);
+
+/* Replace gate `id` of level `level` by *g (a remove followed by an insert
+ * into the same level, checked for conflicts against the other gates).
+ * *out receives the new id.  On error nothing changes. */
+qt_status qt_replace_gate(qt_circuit* c, int32_t level, qt_gate_id id, const qt_gate* g, qt_gate_id* out);
+
+/* Bring the state up to date with all pending edits (update_state, Table 2).
+ * force_full = 0: incremental -- only segments at or after the first edited
+ * one run, each over the partitions its edits (or the dirty partitions
+ * flowing in from earlier segments) can reach (Section III-E).
+ * force_full = 1: every segment over every partition.  Both give the same
+ * bits.  Blocks until the device work is done.  stats may be NULL.  On error
+ * the previous state stays readable and the edits stay pending. */
+qt_status qt_update_state(qt_circuit* c, int32_t force_full, qt_update_stats* stats);
+
+/* Copy amplitudes [first, first + count) of the current state to host memory
+ * (binary64 re/im pairs for QT_C128 and QT_C128_DF, binary32 pairs for
+ * QT_C64).  QT_ERR_STALE while edits are pending; QT_ERR_RANGE if the range
+ * exceeds 2^n. */
+qt_status qt_read_amplitudes(const qt_circuit* c, uint64_t first, uint64_t count, void* host_dst);
+
+/* Same, into a device buffer of the caller (same element format). */
+qt_status qt_read_amplitudes_device(const qt_circuit* c, uint64_t first, uint64_t count, void* device_dst);
+
+/* sum_b |alpha_b|^2 of the current state (Section II-A), reduced with
+ * FP64-class accuracy for every dtype (float-float partial sums, FP64 tree). */
+qt_status qt_norm(const qt_circuit* c, double* out);
+
+/* Options (value semantics):
+ *   "ckpt_interval"  levels per checkpoint segment (>= 1; default 4)
+ *   "fusion"         0: one gate per pass; 1: tile fusion (default)
+ *   "tile_high"      max qubits at or above the tile's low bits per pass (0..7)
+ *   "mem_limit"      device-memory budget in bytes for state + checkpoints (0 = none)
+ *   "kernel_timing"  1: time every fused-pass kernel with CUDA events (stats)
+ *   "dry_run"        1: qt_update_state plans and tracks but launches nothing and
+ *                    allocates nothing (host-logic testing); the device state is
+ *                    marked stale and the next real update runs in full.
+ * Changing ckpt_interval, fusion or tile_high makes the next update full. */
+qt_status qt_set_option(qt_circuit* c, const char* key, int64_t value);
+
+/* Run the circuit's GPU work on `cuda_stream` (a cudaStream_t; NULL = the
+ * library's own stream). */
+qt_status qt_set_stream(qt_circuit* c, void* cuda_stream);
+
+/* Introspection of the last qt_update_state (real or dry run), for tests and
+ * debugging.  For segment `seg`: levels [*first_level, *first_level +
+ * *nlevels); optional out arrays of 2^(n - log2_partition) bytes receive the
+ * segment's forward dirty set F (partitions whose output may have changed)
+ * and worklist W (partitions recomputed), 1 = member. */
+qt_status qt_num_segments(const qt_circuit* c, int32_t* out);
+qt_status qt_segment_info(const qt_circuit* c, int32_t seg, int32_t* first_level, int32_t* nlevels,
+                          int32_t* npasses, uint8_t* dirty_out, uint8_t* worklist_out);
+
+/* Message of the last failed call on c (or of the last failed qt_create when
+ * c is NULL).  Valid until the next call on c. */
+const char* qt_last_error(const qt_circuit* c);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* QTASK_H */

@@ -1,0 +1,893 @@
+// qt_api.cpp -- the C ABI of libqtask.so (include/qtask.h): circuit store and
+// modifiers, checkpoint store, dirty-partition tracker and scheduler.
+//
+// qTask references: programming model and modifiers, Section III-B and
+// Table 2; a modifier that makes a gate share a qubit with its net throws,
+// Section III-B; frontiers (inserted gates' partitions, successors of removed
+// ones) and reachable partitions, Section III-E; per-net state vectors kept
+// for incrementality, Section III-F.
+//
+// Design (GB300): the circuit is cut into segments of `ckpt_interval`
+// levels; the state at every segment boundary is a device-resident
+// checkpoint slab.  Each segment is planned into fused passes (qt_plan.cpp).
+// On update, a segment whose plan and input are unchanged is skipped; for the
+// others the tracker seeds the partitions touched by the passes that differ
+// between the old and new plan, propagates them forward through the coupling
+// of every pass (the forward cone F = partitions whose output may change) and
+// closes F under all couplings of the segment (the worklist W).  The
+// segment's first pass reads checkpoint s and writes checkpoint s+1 for the
+// groups of W, later passes run in place on checkpoint s+1.  Partitions
+// outside W keep their bits, partitions of W \ F are recomputed to the same
+// bits, so the result equals a full re-simulation bit for bit.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "qt_internal.h"
+
+using namespace qt;
+
+namespace {
+thread_local std::string g_create_error;
+
+int tile_low_default(int dtype) { return dtype == QT_C64 ? 7 : 6; }
+
+struct Launch {
+    int kind;  // 0 = pass, 1 = copy partitions
+    int seg;
+    int64_t pass_idx;
+    DevPass dp;
+    size_t wl_offset;  // into the worklist buffer (in entries)
+    uint32_t ngroups;
+    bool null_worklist;
+    bool out_of_place;
+    uint64_t parts_processed;
+    int ngates;
+};
+}  // namespace
+
+struct qt_circuit {
+    int n = 0, p = 0, dtype = 0;
+    std::vector<Level> levels;
+    qt_gate_id next_id = 1;
+    bool pending = false;
+
+    // options
+    int ckpt_interval = 4;
+    bool fusion = true;
+    int tile_high = 6;
+    int64_t mem_limit = 0;
+    bool kernel_timing = false;
+    bool dry_run = false;
+
+    // committed plan (matches the slabs when device_valid)
+    bool have_plan = false;
+    PlanParams plan_pp;
+    int plan_G = 0;
+    std::vector<SegPlan> plans;
+    std::vector<std::vector<Bitset>> supps;
+    bool device_valid = false;
+    bool state_stale = false;  // set by dry runs
+
+    // introspection of the last update
+    std::vector<Bitset> last_F, last_W;
+
+    // device
+    bool device_ready = false;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    std::vector<void*> slabs;
+    DevOp* d_ops = nullptr;
+    size_t d_ops_cap = 0;
+    uint32_t* d_wl = nullptr;
+    size_t d_wl_cap = 0;
+    DevOp* h_ops = nullptr;  // pinned staging
+    size_t h_ops_cap = 0;
+    uint32_t* h_wl = nullptr;
+    size_t h_wl_cap = 0;
+    double* d_norm_partials = nullptr;
+    double* d_norm_out = nullptr;
+    int norm_cap = 0;
+    void* d_read = nullptr;
+    size_t d_read_cap = 0;
+    cudaEvent_t ev_begin = nullptr, ev_end = nullptr;
+    std::vector<cudaEvent_t> ev_pool;
+
+    std::string err;
+
+    uint64_t namps() const { return uint64_t(1) << n; }
+    uint32_t nparts() const { return uint32_t(1) << (n - p); }
+    size_t state_bytes() const { return size_t(namps()) * bytes_per_amp(dtype); }
+};
+
+namespace {
+
+qt_status fail(qt_circuit* c, qt_status s, const std::string& msg) {
+    if (c) c->err = msg;
+    return s;
+}
+
+qt_status cuda_fail(qt_circuit* c, int e, const char* what) {
+    return fail(c, QT_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(cudaError_t(e)));
+}
+
+int lowest_qubit(const qt_gate& g) {
+    int m = 1 << 30;
+    for (int k = 0; k < g.ntarget; ++k) m = std::min(m, g.target[k]);
+    for (int k = 0; k < g.ncontrol; ++k) m = std::min(m, g.control[k]);
+    return m;
+}
+
+uint64_t level_qubits(const Level& L, qt_gate_id skip) {
+    uint64_t m = 0;
+    for (const Gate& g : L.gates)
+        if (g.id != skip) m |= gate_qubit_mask(g.g);
+    return m;
+}
+
+void insert_sorted(Level& L, const Gate& g) {
+    int key = lowest_qubit(g.g);
+    auto it = std::find_if(L.gates.begin(), L.gates.end(), [&](const Gate& x) { return lowest_qubit(x.g) > key; });
+    L.gates.insert(it, g);
+}
+
+void free_device(qt_circuit* c) {
+    if (!c->device_ready) return;
+    cudaStreamSynchronize(c->stream);
+    for (void* s : c->slabs) cudaFree(s);
+    c->slabs.clear();
+    cudaFree(c->d_ops);
+    cudaFree(c->d_wl);
+    cudaFreeHost(c->h_ops);
+    cudaFreeHost(c->h_wl);
+    cudaFree(c->d_norm_partials);
+    cudaFree(c->d_norm_out);
+    cudaFree(c->d_read);
+    if (c->ev_begin) cudaEventDestroy(c->ev_begin);
+    if (c->ev_end) cudaEventDestroy(c->ev_end);
+    for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
+    c->ev_pool.clear();
+    if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+    c->device_ready = false;
+    c->device_valid = false;
+}
+
+// Create the stream and slab 0 (|0...0>).
+qt_status ensure_device(qt_circuit* c) {
+    if (c->device_ready) return QT_OK;
+    int ndev = 0;
+    cudaError_t e = cudaGetDeviceCount(&ndev);
+    if (e != cudaSuccess || ndev == 0)
+        return fail(c, QT_ERR_CUDA, std::string("no CUDA device available: ") + cudaGetErrorString(e));
+    if (c->mem_limit > 0 && int64_t(c->state_bytes()) > c->mem_limit)
+        return fail(c, QT_ERR_OOM, "mem_limit below one state vector");
+    if (!c->stream) {
+        e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) return cuda_fail(c, e, "cudaStreamCreate");
+        c->own_stream = true;
+    }
+    if ((e = cudaEventCreate(&c->ev_begin)) != cudaSuccess) return cuda_fail(c, e, "cudaEventCreate");
+    if ((e = cudaEventCreate(&c->ev_end)) != cudaSuccess) return cuda_fail(c, e, "cudaEventCreate");
+    void* s0 = nullptr;
+    e = cudaMalloc(&s0, c->state_bytes());
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(c, QT_ERR_OOM, "cudaMalloc of the state vector failed");
+    }
+    c->slabs.push_back(s0);
+    int rc = launch_init_zero_state(c->dtype, s0, c->namps(), c->stream);
+    if (rc) return cuda_fail(c, rc, "init state");
+    c->device_ready = true;
+    c->device_valid = false;
+    return QT_OK;
+}
+
+qt_status ensure_slabs(qt_circuit* c, size_t nslabs) {
+    if (c->mem_limit > 0 && int64_t(nslabs * c->state_bytes()) > c->mem_limit)
+        return fail(c, QT_ERR_OOM,
+                    "checkpoints need " + std::to_string(nslabs) + " state vectors, above mem_limit");
+    while (c->slabs.size() < nslabs) {
+        void* s = nullptr;
+        cudaError_t e = cudaMalloc(&s, c->state_bytes());
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return fail(c, QT_ERR_OOM, "cudaMalloc of a checkpoint slab failed");
+        }
+        c->slabs.push_back(s);
+    }
+    return QT_OK;
+}
+
+template <class T>
+qt_status grow_device(qt_circuit* c, T** d, size_t* cap, size_t need) {
+    if (need <= *cap) return QT_OK;
+    size_t ncap = std::max<size_t>(need, *cap * 2);
+    cudaFree(*d);
+    *d = nullptr;
+    *cap = 0;
+    cudaError_t e = cudaMalloc(reinterpret_cast<void**>(d), ncap * sizeof(T));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(c, QT_ERR_OOM, "cudaMalloc of a plan buffer failed");
+    }
+    *cap = ncap;
+    return QT_OK;
+}
+
+template <class T>
+qt_status grow_host(qt_circuit* c, T** h, size_t* cap, size_t need) {
+    if (need <= *cap) return QT_OK;
+    size_t ncap = std::max<size_t>(need, *cap * 2);
+    cudaFreeHost(*h);
+    *h = nullptr;
+    *cap = 0;
+    cudaError_t e = cudaMallocHost(reinterpret_cast<void**>(h), ncap * sizeof(T));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(c, QT_ERR_OOM, "cudaMallocHost of a staging buffer failed");
+    }
+    *cap = ncap;
+    return QT_OK;
+}
+
+PlanParams make_params(const qt_circuit* c) {
+    PlanParams pp;
+    pp.n = c->n;
+    pp.p = c->p;
+    pp.lt = std::min(c->p, tile_low_default(c->dtype));
+    pp.nh_max = std::max(0, std::min(c->tile_high, c->n - pp.lt));
+    pp.fusion = c->fusion;
+    return pp;
+}
+
+bool same_params(const PlanParams& a, const PlanParams& b) {
+    return a.n == b.n && a.p == b.p && a.lt == b.lt && a.nh_max == b.nh_max && a.fusion == b.fusion;
+}
+
+DevOp encode_op(int dtype, const Pass& ps, const HostOp& op) {
+    DevOp d;
+    std::memset(&d, 0, sizeof d);
+    auto loc = [&](int q) -> int {
+        if (q < ps.lt) return q;
+        for (int k = 0; k < ps.nh; ++k)
+            if (ps.h[k] == q) return ps.lt + k;
+        return -1;
+    };
+    uint64_t tile_mask = (uint64_t(1) << ps.lt) - 1;
+    for (int k = 0; k < ps.nh; ++k) tile_mask |= uint64_t(1) << ps.h[k];
+    d.kind = op.kind;
+    d.cm_glob = op.cmask & ~tile_mask;
+    std::vector<std::pair<int, int>> fixed;  // (tile-local position, value)
+    for (int q = 0; q < 64; ++q)
+        if (((op.cmask & tile_mask) >> q) & 1) fixed.push_back({loc(q), 1});
+    d.b0 = op.q0 >= 0 ? loc(op.q0) : -1;
+    d.gq = op.q0;
+    d.b1 = -1;
+    switch (op.kind) {
+        case OP_DENSE: case OP_REAL: case OP_X: case OP_ANTI:
+            fixed.push_back({d.b0, 0});
+            break;
+        case OP_SWAP:
+            d.b1 = loc(op.q1);
+            fixed.push_back({d.b0, 1});
+            fixed.push_back({d.b1, 0});
+            break;
+        case OP_PHASE: {
+            const double re = op.m[0], im = op.m[1];
+            d.b1 = PH_GENERAL;
+            if (re == -1.0 && im == 0.0) d.b1 = PH_NEG;
+            else if (re == 0.0 && im == 1.0) d.b1 = PH_POS_I;
+            else if (re == 0.0 && im == -1.0) d.b1 = PH_NEG_I;
+            break;
+        }
+        default: break;
+    }
+    std::sort(fixed.begin(), fixed.end());
+    d.nfix = uint8_t(fixed.size());
+    d.fixval = 0;
+    for (size_t k = 0; k < fixed.size(); ++k) {
+        d.fixpos[k] = int8_t(fixed[k].first);
+        if (fixed[k].second) d.fixval |= uint8_t(1u << k);
+    }
+    encode_matrix(dtype, op, &d);
+    return d;
+}
+
+cudaEvent_t pool_event(qt_circuit* c, size_t i) {
+    while (c->ev_pool.size() <= i) {
+        cudaEvent_t e;
+        if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+        c->ev_pool.push_back(e);
+    }
+    return c->ev_pool[i];
+}
+
+qt_status do_update(qt_circuit* c, int force_full, qt_update_stats* stats) {
+    auto t0 = std::chrono::steady_clock::now();
+    qt_update_stats st;
+    std::memset(&st, 0, sizeof st);
+    st.gpu_ms = -1.0;
+    st.pass_kernel_ms = -1.0;
+
+    // ---- plan
+    const PlanParams pp = make_params(c);
+    const int G = c->ckpt_interval;
+    const int L = int(c->levels.size());
+    const int S = (L + G - 1) / G;
+    std::vector<SegPlan> nplans(S);
+    std::vector<std::vector<Bitset>> nsupps(S);
+    const uint32_t nparts = c->nparts();
+    int64_t ngates_total = 0;
+    for (int s = 0; s < S; ++s) {
+        std::vector<const qt_gate*> gl;
+        const int l0 = s * G, l1 = std::min(L, (s + 1) * G);
+        for (int l = l0; l < l1; ++l)
+            for (const Gate& g : c->levels[l].gates) gl.push_back(&g.g);
+        ngates_total += int64_t(gl.size());
+        nplans[s] = plan_segment(gl, pp);
+        nplans[s].first_level = l0;
+        nplans[s].nlevels = l1 - l0;
+        for (const Pass& ps : nplans[s].passes) nsupps[s].push_back(pass_support(ps, nparts));
+    }
+    const bool params_changed = !c->have_plan || !same_params(pp, c->plan_pp) || G != c->plan_G;
+    bool full = force_full || params_changed || (!c->dry_run && !c->device_valid);
+
+    // ---- device
+    if (!c->dry_run) {
+        qt_status rs = ensure_device(c);
+        if (rs != QT_OK) return rs;
+        rs = ensure_slabs(c, size_t(S) + 1);
+        if (rs != QT_OK) return rs;
+        if (!c->device_valid) full = true;
+    }
+
+    // ---- track and schedule
+    std::vector<Launch> launches;
+    std::vector<DevOp> hops;
+    std::vector<uint32_t> hwl;
+    std::vector<Bitset> lastF(S), lastW(S);
+    Bitset dirty_in;
+    dirty_in.resize(nparts);
+    const int old_S = c->have_plan ? int(c->plans.size()) : 0;
+    for (int s = 0; s < S; ++s) {
+        const SegPlan& np = nplans[s];
+        const std::vector<Bitset>& sup = nsupps[s];
+        Bitset F, W;
+        F.resize(nparts);
+        W.resize(nparts);
+        if (full || s >= old_S) {
+            F.fill();
+            W.fill();
+        } else {
+            const SegPlan& op = c->plans[s];
+            const std::vector<Bitset>& osup = c->supps[s];
+            const size_t lo = op.passes.size(), ln = np.passes.size();
+            size_t j = 0;
+            while (j < lo && j < ln && op.passes[j].same_as(np.passes[j])) ++j;
+            size_t k = 0;
+            while (k < lo - j && k < ln - j && op.passes[lo - 1 - k].same_as(np.passes[ln - 1 - k])) ++k;
+            const bool same_plan = (j == lo && j == ln);
+            if (!(same_plan && !dirty_in.any())) {
+                Bitset seeds;
+                seeds.resize(nparts);
+                for (size_t i = j; i < lo - k; ++i) seeds.or_with(osup[i]);
+                for (size_t i = j; i < ln - k; ++i) seeds.or_with(sup[i]);
+                Bitset D = dirty_in;
+                for (size_t i = 0; i < ln; ++i) {
+                    if (i == j) D.or_with(seeds);
+                    close_forward(&D, np.passes[i], sup[i]);
+                }
+                if (j >= ln) D.or_with(seeds);
+                F = D;
+                W = F;
+                close_all(&W, np.passes, sup);
+            }
+        }
+        lastF[s] = F;
+        lastW[s] = W;
+        dirty_in = F;
+        if (!W.any()) continue;
+        st.segments_run += 1;
+        if (np.passes.empty()) {
+            Launch ln{};
+            ln.kind = 1;
+            ln.seg = s;
+            ln.wl_offset = hwl.size();
+            for (uint32_t q = 0; q < nparts; ++q)
+                if (W.get(q)) hwl.push_back(q);
+            ln.ngroups = uint32_t(hwl.size() - ln.wl_offset);
+            ln.parts_processed = ln.ngroups;
+            launches.push_back(ln);
+            continue;
+        }
+        for (size_t i = 0; i < np.passes.size(); ++i) {
+            const Pass& ps = np.passes[i];
+            Launch ln{};
+            ln.kind = 0;
+            ln.seg = s;
+            ln.pass_idx = int64_t(i);
+            ln.out_of_place = (i == 0);
+            ln.ngates = ps.ngates;
+            // groups: members of W (first pass) or of W n supp (later passes)
+            Bitset T = W;
+            if (i > 0)
+                for (size_t w = 0; w < T.w.size(); ++w) T.w[w] &= sup[i].w[w];
+            if (!T.any()) continue;
+            const uint32_t gcount_all = nparts >> __builtin_popcount(ps.M);
+            ln.wl_offset = hwl.size();
+            if (T.all()) {
+                ln.null_worklist = true;
+                ln.ngroups = gcount_all;
+            } else {
+                ln.null_worklist = false;
+                Bitset mark;
+                mark.resize(nparts);
+                for (uint32_t q = 0; q < nparts; ++q) {
+                    if (!T.get(q)) continue;
+                    uint32_t g = q & ~ps.M;
+                    if (!mark.get(g)) {
+                        mark.set(g);
+                        hwl.push_back(g);
+                    }
+                }
+                ln.ngroups = uint32_t(hwl.size() - ln.wl_offset);
+            }
+            ln.parts_processed = uint64_t(ln.ngroups) << __builtin_popcount(ps.M);
+            DevPass& dp = ln.dp;
+            std::memset(&dp, 0, sizeof dp);
+            dp.p = c->p;
+            dp.lt = ps.lt;
+            dp.nh = ps.nh;
+            dp.nins = 0;
+            for (int h = 0; h < ps.nh; ++h) {
+                dp.h[h] = ps.h[h];
+                if (ps.h[h] < c->p) dp.ins[dp.nins++] = ps.h[h];
+            }
+            dp.tpg_log2 = c->p - ps.lt - dp.nins;
+            dp.nops = int32_t(ps.ops.size());
+            dp.M = ps.M;
+            dp.npart_log2 = c->n - c->p;
+            dp.op_offset = int64_t(hops.size());
+            for (const HostOp& o : ps.ops) hops.push_back(encode_op(c->dtype, ps, o));
+            launches.push_back(ln);
+        }
+    }
+
+    // ---- stats (plan side)
+    st.segments_total = S;
+    st.gates_total = int32_t(ngates_total);
+    for (int s = 0; s < S; ++s) {
+        st.passes_total += int32_t(nplans[s].passes.size());
+        st.partition_passes_total += int64_t(nplans[s].passes.size()) * nparts;
+    }
+    const uint64_t part_amps = uint64_t(1) << c->p;
+    const uint64_t bpa = bytes_per_amp(c->dtype);
+    for (const Launch& ln : launches) {
+        st.launches += 1;
+        if (ln.kind == 0) {
+            st.passes_run += 1;
+            st.partition_passes_run += int64_t(ln.parts_processed);
+            st.amp_updates += ln.parts_processed * part_amps * uint64_t(ln.ngates);
+        }
+        st.hbm_bytes += 2 * bpa * ln.parts_processed * part_amps;
+    }
+    st.clean_fraction =
+        st.partition_passes_total ? 1.0 - double(st.partition_passes_run) / double(st.partition_passes_total) : 0.0;
+
+    // ---- run
+    if (!c->dry_run) {
+        qt_status rs;
+        if ((rs = grow_device(c, &c->d_ops, &c->d_ops_cap, std::max<size_t>(hops.size(), 1))) != QT_OK) return rs;
+        if ((rs = grow_device(c, &c->d_wl, &c->d_wl_cap, std::max<size_t>(hwl.size(), 1))) != QT_OK) return rs;
+        if ((rs = grow_host(c, &c->h_ops, &c->h_ops_cap, std::max<size_t>(hops.size(), 1))) != QT_OK) return rs;
+        if ((rs = grow_host(c, &c->h_wl, &c->h_wl_cap, std::max<size_t>(hwl.size(), 1))) != QT_OK) return rs;
+        st.h2d_bytes = hops.size() * sizeof(DevOp) + hwl.size() * sizeof(uint32_t);
+        if (!hops.empty()) std::memcpy(c->h_ops, hops.data(), hops.size() * sizeof(DevOp));
+        if (!hwl.empty()) std::memcpy(c->h_wl, hwl.data(), hwl.size() * sizeof(uint32_t));
+        cudaError_t e;
+        c->device_valid = false;  // until the whole schedule has run
+        if ((e = cudaEventRecord(c->ev_begin, c->stream)) != cudaSuccess) return cuda_fail(c, e, "event");
+        if (!hops.empty() &&
+            (e = cudaMemcpyAsync(c->d_ops, c->h_ops, hops.size() * sizeof(DevOp), cudaMemcpyHostToDevice,
+                                 c->stream)) != cudaSuccess)
+            return cuda_fail(c, e, "upload ops");
+        if (!hwl.empty() &&
+            (e = cudaMemcpyAsync(c->d_wl, c->h_wl, hwl.size() * sizeof(uint32_t), cudaMemcpyHostToDevice,
+                                 c->stream)) != cudaSuccess)
+            return cuda_fail(c, e, "upload worklists");
+        size_t evi = 0;
+        for (const Launch& ln : launches) {
+            void* src = c->slabs[ln.seg];
+            void* dst = c->slabs[ln.seg + 1];
+            int rc;
+            if (ln.kind == 1) {
+                rc = launch_copy_parts(c->dtype, dst, src, c->p, c->d_wl + ln.wl_offset, ln.ngroups, c->stream);
+            } else {
+                cudaEvent_t e0 = nullptr, e1 = nullptr;
+                if (c->kernel_timing) {
+                    e0 = pool_event(c, evi++);
+                    e1 = pool_event(c, evi++);
+                    if (!e0 || !e1) return fail(c, QT_ERR_CUDA, "event pool");
+                    cudaEventRecord(e0, c->stream);
+                }
+                rc = launch_pass(c->dtype, dst, ln.out_of_place ? src : dst, ln.dp, c->d_ops,
+                                 ln.null_worklist ? nullptr : c->d_wl + ln.wl_offset, ln.ngroups, c->stream);
+                if (c->kernel_timing) cudaEventRecord(e1, c->stream);
+            }
+            if (rc) return cuda_fail(c, rc, "kernel launch");
+        }
+        if ((e = cudaEventRecord(c->ev_end, c->stream)) != cudaSuccess) return cuda_fail(c, e, "event");
+        if ((e = cudaStreamSynchronize(c->stream)) != cudaSuccess) return cuda_fail(c, e, "update_state");
+        float ms = 0.0f;
+        if (cudaEventElapsedTime(&ms, c->ev_begin, c->ev_end) == cudaSuccess) st.gpu_ms = ms;
+        if (c->kernel_timing) {
+            double tot = 0.0;
+            size_t k = 0;
+            for (const Launch& ln : launches) {
+                if (ln.kind != 0) continue;
+                float km = 0.0f;
+                cudaEventElapsedTime(&km, c->ev_pool[k], c->ev_pool[k + 1]);
+                k += 2;
+                tot += km;
+                st.pass_kernel_launches += 1;
+                st.pass_kernel_bytes += 2 * bpa * ln.parts_processed * part_amps;
+            }
+            st.pass_kernel_ms = tot;
+        }
+        c->device_valid = true;
+        c->state_stale = false;
+    } else {
+        c->device_valid = false;
+        c->state_stale = true;
+        // the slabs beyond the committed plan hold nothing useful now
+    }
+
+    // ---- commit
+    c->plans = std::move(nplans);
+    c->supps = std::move(nsupps);
+    c->plan_pp = pp;
+    c->plan_G = G;
+    c->have_plan = true;
+    c->last_F = std::move(lastF);
+    c->last_W = std::move(lastW);
+    c->pending = false;
+    if (!c->dry_run && c->device_ready) {
+        // release slabs the plan no longer uses
+        while (c->slabs.size() > size_t(S) + 1) {
+            cudaFree(c->slabs.back());
+            c->slabs.pop_back();
+        }
+    }
+    st.host_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    if (stats) *stats = st;
+    return QT_OK;
+}
+
+const void* final_state(const qt_circuit* c) { return c->slabs[c->have_plan ? c->plans.size() : 0]; }
+
+qt_status check_readable(qt_circuit* c) {
+    if (c->pending) return fail(c, QT_ERR_STALE, "edits are pending: call qt_update_state first");
+    if (c->state_stale) return fail(c, QT_ERR_STALE, "the last update was a dry run: the state was not computed");
+    qt_status rs = ensure_device(c);
+    if (rs != QT_OK) return rs;
+    if (c->have_plan && !c->device_valid && !c->plans.empty())
+        return fail(c, QT_ERR_STALE, "the device state is not valid (a previous update failed)");
+    return QT_OK;
+}
+
+}  // namespace
+
+// ===================================================================== ABI ==
+#define QT_GUARD_BEGIN try {
+#define QT_GUARD_END(c)                                                    \
+    }                                                                      \
+    catch (const std::bad_alloc&) {                                        \
+        return fail(c, QT_ERR_OOM, "host allocation failed");              \
+    }                                                                      \
+    catch (...) {                                                          \
+        return fail(c, QT_ERR_ARG, "internal error (unexpected exception)"); \
+    }
+
+extern "C" {
+
+qt_status qt_create(int32_t n_qubits, int32_t dtype, int32_t log2_partition, qt_circuit** out) {
+    if (!out) {
+        g_create_error = "out is NULL";
+        return QT_ERR_ARG;
+    }
+    *out = nullptr;
+    if (n_qubits < 1 || n_qubits > kMaxQubits) {
+        g_create_error = "n_qubits must be in [1, 34]";
+        return QT_ERR_ARG;
+    }
+    if (dtype != QT_C128 && dtype != QT_C64 && dtype != QT_C128_DF) {
+        g_create_error = "unknown dtype";
+        return QT_ERR_ARG;
+    }
+    if (log2_partition < 0 || log2_partition > n_qubits || n_qubits - log2_partition > 30) {
+        g_create_error = "log2_partition must be in [max(0, n-30), n]";
+        return QT_ERR_ARG;
+    }
+    try {
+        qt_circuit* c = new qt_circuit();
+        c->n = n_qubits;
+        c->dtype = dtype;
+        c->p = log2_partition;
+        *out = c;
+        return QT_OK;
+    } catch (...) {
+        g_create_error = "host allocation failed";
+        return QT_ERR_OOM;
+    }
+}
+
+qt_status qt_destroy(qt_circuit* c) {
+    if (!c) return QT_OK;
+    free_device(c);
+    delete c;
+    return QT_OK;
+}
+
+qt_status qt_num_levels(const qt_circuit* c, int32_t* out) {
+    if (!c || !out) return QT_ERR_ARG;
+    *out = int32_t(c->levels.size());
+    return QT_OK;
+}
+
+qt_status qt_num_gates(const qt_circuit* c, int64_t* out) {
+    if (!c || !out) return QT_ERR_ARG;
+    int64_t k = 0;
+    for (const Level& L : c->levels) k += int64_t(L.gates.size());
+    *out = k;
+    return QT_OK;
+}
+
+qt_status qt_insert_level(qt_circuit* c, int32_t pos) {
+    if (!c) return QT_ERR_ARG;
+    QT_GUARD_BEGIN
+    if (pos < 0 || pos > int32_t(c->levels.size())) return fail(c, QT_ERR_RANGE, "level position out of range");
+    c->levels.insert(c->levels.begin() + pos, Level());
+    c->pending = true;
+    return QT_OK;
+    QT_GUARD_END(c)
+}
+
+qt_status qt_remove_level(qt_circuit* c, int32_t pos) {
+    if (!c) return QT_ERR_ARG;
+    QT_GUARD_BEGIN
+    if (pos < 0 || pos >= int32_t(c->levels.size())) return fail(c, QT_ERR_RANGE, "level out of range");
+    c->levels.erase(c->levels.begin() + pos);
+    c->pending = true;
+    return QT_OK;
+    QT_GUARD_END(c)
+}
+
+qt_status qt_insert_gate(qt_circuit* c, int32_t level, const qt_gate* g, qt_gate_id* out) {
+    if (!c) return QT_ERR_ARG;
+    if (!g) return fail(c, QT_ERR_ARG, "gate is NULL");
+    QT_GUARD_BEGIN
+    std::string err;
+    if (!check_gate(*g, c->n, &err)) return fail(c, QT_ERR_ARG, err);
+    if (level < 0 || level >= int32_t(c->levels.size())) return fail(c, QT_ERR_RANGE, "level out of range");
+    Level& L = c->levels[level];
+    if (level_qubits(L, 0) & gate_qubit_mask(*g))
+        return fail(c, QT_ERR_CONFLICT, "gate shares a qubit with a gate of level " + std::to_string(level));
+    Gate ng;
+    ng.g = *g;
+    ng.id = c->next_id++;
+    insert_sorted(L, ng);
+    c->pending = true;
+    if (out) *out = ng.id;
+    return QT_OK;
+    QT_GUARD_END(c)
+}
+
+qt_status qt_remove_gate(qt_circuit* c, int32_t level, qt_gate_id id) {
+    if (!c) return QT_ERR_ARG;
+    QT_GUARD_BEGIN
+    if (level < 0 || level >= int32_t(c->levels.size())) return fail(c, QT_ERR_RANGE, "level out of range");
+    Level& L = c->levels[level];
+    auto it = std::find_if(L.gates.begin(), L.gates.end(), [&](const Gate& x) { return x.id == id; });
+    if (it == L.gates.end()) return fail(c, QT_ERR_NOT_FOUND, "no gate with that id in that level");
+    L.gates.erase(it);
+    c->pending = true;
+    return QT_OK;
+    QT_GUARD_END(c)
+}
+
+qt_status qt_replace_gate(qt_circuit* c, int32_t level, qt_gate_id id, const qt_gate* g, qt_gate_id* out) {
+    if (!c) return QT_ERR_ARG;
+    if (!g) return fail(c, QT_ERR_ARG, "gate is NULL");
+    QT_GUARD_BEGIN
+    std::string err;
+    if (!check_gate(*g, c->n, &err)) return fail(c, QT_ERR_ARG, err);
+    if (level < 0 || level >= int32_t(c->levels.size())) return fail(c, QT_ERR_RANGE, "level out of range");
+    Level& L = c->levels[level];
+    auto it = std::find_if(L.gates.begin(), L.gates.end(), [&](const Gate& x) { return x.id == id; });
+    if (it == L.gates.end()) return fail(c, QT_ERR_NOT_FOUND, "no gate with that id in that level");
+    if (level_qubits(L, id) & gate_qubit_mask(*g))
+        return fail(c, QT_ERR_CONFLICT, "replacement shares a qubit with another gate of the level");
+    L.gates.erase(it);
+    Gate ng;
+    ng.g = *g;
+    ng.id = c->next_id++;
+    insert_sorted(L, ng);
+    c->pending = true;
+    if (out) *out = ng.id;
+    return QT_OK;
+    QT_GUARD_END(c)
+}
+
+qt_status qt_update_state(qt_circuit* c, int32_t force_full, qt_update_stats* stats) {
+    if (!c) return QT_ERR_ARG;
+    QT_GUARD_BEGIN
+    return do_update(c, force_full, stats);
+    QT_GUARD_END(c)
+}
+
+qt_status qt_read_amplitudes(const qt_circuit* cc, uint64_t first, uint64_t count, void* host_dst) {
+    qt_circuit* c = const_cast<qt_circuit*>(cc);
+    if (!c) return QT_ERR_ARG;
+    QT_GUARD_BEGIN
+    if (count && !host_dst) return fail(c, QT_ERR_ARG, "host_dst is NULL");
+    if (first > c->namps() || count > c->namps() - first) return fail(c, QT_ERR_RANGE, "amplitude range");
+    qt_status rs = check_readable(c);
+    if (rs != QT_OK) return rs;
+    if (count == 0) return QT_OK;
+    const void* src = final_state(c);
+    cudaError_t e;
+    if (c->dtype != QT_C128_DF) {
+        const size_t b = bytes_per_amp(c->dtype);
+        e = cudaMemcpyAsync(host_dst, static_cast<const char*>(src) + first * b, count * b, cudaMemcpyDeviceToHost,
+                            c->stream);
+        if (e != cudaSuccess) return cuda_fail(c, e, "read amplitudes");
+    } else {
+        const uint64_t chunk = uint64_t(1) << 22;  // amplitudes per staging round (64 MiB)
+        const size_t need = size_t(std::min(count, chunk)) * 16;
+        if (c->d_read_cap < need) {
+            cudaFree(c->d_read);
+            c->d_read = nullptr;
+            c->d_read_cap = 0;
+            if ((e = cudaMalloc(&c->d_read, need)) != cudaSuccess) {
+                cudaGetLastError();
+                return fail(c, QT_ERR_OOM, "staging buffer");
+            }
+            c->d_read_cap = need;
+        }
+        for (uint64_t off = 0; off < count; off += chunk) {
+            const uint64_t m = std::min(chunk, count - off);
+            int rc = launch_read_convert(c->dtype, c->d_read, src, first + off, m, c->stream);
+            if (rc) return cuda_fail(c, rc, "convert");
+            e = cudaMemcpyAsync(static_cast<char*>(host_dst) + off * 16, c->d_read, m * 16, cudaMemcpyDeviceToHost,
+                                c->stream);
+            if (e != cudaSuccess) return cuda_fail(c, e, "read amplitudes");
+        }
+    }
+    if ((e = cudaStreamSynchronize(c->stream)) != cudaSuccess) return cuda_fail(c, e, "read amplitudes");
+    return QT_OK;
+    QT_GUARD_END(c)
+}
+
+qt_status qt_read_amplitudes_device(const qt_circuit* cc, uint64_t first, uint64_t count, void* device_dst) {
+    qt_circuit* c = const_cast<qt_circuit*>(cc);
+    if (!c) return QT_ERR_ARG;
+    QT_GUARD_BEGIN
+    if (count && !device_dst) return fail(c, QT_ERR_ARG, "device_dst is NULL");
+    if (first > c->namps() || count > c->namps() - first) return fail(c, QT_ERR_RANGE, "amplitude range");
+    qt_status rs = check_readable(c);
+    if (rs != QT_OK) return rs;
+    int rc = launch_read_convert(c->dtype, device_dst, final_state(c), first, count, c->stream);
+    if (rc) return cuda_fail(c, rc, "read amplitudes");
+    cudaError_t e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "read amplitudes");
+    return QT_OK;
+    QT_GUARD_END(c)
+}
+
+qt_status qt_norm(const qt_circuit* cc, double* out) {
+    qt_circuit* c = const_cast<qt_circuit*>(cc);
+    if (!c) return QT_ERR_ARG;
+    if (!out) return fail(c, QT_ERR_ARG, "out is NULL");
+    QT_GUARD_BEGIN
+    qt_status rs = check_readable(c);
+    if (rs != QT_OK) return rs;
+    const int np = norm_partials_needed(c->namps());
+    cudaError_t e;
+    if (c->norm_cap < np) {
+        cudaFree(c->d_norm_partials);
+        c->d_norm_partials = nullptr;
+        c->norm_cap = 0;
+        if ((e = cudaMalloc(&c->d_norm_partials, sizeof(double) * np)) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(c, QT_ERR_OOM, "norm scratch");
+        }
+        c->norm_cap = np;
+    }
+    if (!c->d_norm_out && (e = cudaMalloc(&c->d_norm_out, sizeof(double))) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(c, QT_ERR_OOM, "norm scratch");
+    }
+    int rc = launch_norm(c->dtype, final_state(c), c->namps(), c->d_norm_partials, np, c->d_norm_out, c->stream);
+    if (rc) return cuda_fail(c, rc, "norm");
+    e = cudaMemcpyAsync(out, c->d_norm_out, sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "norm");
+    if ((e = cudaStreamSynchronize(c->stream)) != cudaSuccess) return cuda_fail(c, e, "norm");
+    return QT_OK;
+    QT_GUARD_END(c)
+}
+
+qt_status qt_set_option(qt_circuit* c, const char* key, int64_t value) {
+    if (!c) return QT_ERR_ARG;
+    if (!key) return fail(c, QT_ERR_ARG, "key is NULL");
+    std::string k(key);
+    if (k == "ckpt_interval") {
+        if (value < 1 || value > (1 << 20)) return fail(c, QT_ERR_ARG, "ckpt_interval must be >= 1");
+        c->ckpt_interval = int(value);
+    } else if (k == "fusion") {
+        c->fusion = value != 0;
+    } else if (k == "tile_high") {
+        if (value < 0 || value > kMaxTileHigh) return fail(c, QT_ERR_ARG, "tile_high must be in [0, 7]");
+        if (tile_low_default(c->dtype) + value > (c->dtype == QT_C64 ? 13 : 12))
+            return fail(c, QT_ERR_ARG, "tile too large for shared memory");
+        c->tile_high = int(value);
+    } else if (k == "mem_limit") {
+        if (value < 0) return fail(c, QT_ERR_ARG, "mem_limit must be >= 0");
+        c->mem_limit = value;
+    } else if (k == "kernel_timing") {
+        c->kernel_timing = value != 0;
+    } else if (k == "dry_run") {
+        c->dry_run = value != 0;
+    } else {
+        return fail(c, QT_ERR_ARG, "unknown option " + k);
+    }
+    return QT_OK;
+}
+
+qt_status qt_set_stream(qt_circuit* c, void* cuda_stream) {
+    if (!c) return QT_ERR_ARG;
+    if (c->device_ready) cudaStreamSynchronize(c->stream);
+    if (c->own_stream && c->stream) {
+        cudaStreamDestroy(c->stream);
+        c->own_stream = false;
+    }
+    c->stream = static_cast<cudaStream_t>(cuda_stream);
+    if (!c->stream && c->device_ready) {
+        if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess)
+            return fail(c, QT_ERR_CUDA, "cudaStreamCreate");
+        c->own_stream = true;
+    }
+    return QT_OK;
+}
+
+qt_status qt_num_segments(const qt_circuit* c, int32_t* out) {
+    if (!c || !out) return QT_ERR_ARG;
+    *out = c->have_plan ? int32_t(c->plans.size()) : 0;
+    return QT_OK;
+}
+
+qt_status qt_segment_info(const qt_circuit* cc, int32_t seg, int32_t* first_level, int32_t* nlevels,
+                          int32_t* npasses, uint8_t* dirty_out, uint8_t* worklist_out) {
+    qt_circuit* c = const_cast<qt_circuit*>(cc);
+    if (!c) return QT_ERR_ARG;
+    if (!c->have_plan || seg < 0 || seg >= int32_t(c->plans.size()))
+        return fail(c, QT_ERR_RANGE, "segment out of range");
+    const SegPlan& sp = c->plans[seg];
+    if (first_level) *first_level = sp.first_level;
+    if (nlevels) *nlevels = sp.nlevels;
+    if (npasses) *npasses = int32_t(sp.passes.size());
+    const uint32_t np = c->nparts();
+    for (uint32_t q = 0; q < np; ++q) {
+        if (dirty_out) dirty_out[q] = c->last_F[seg].get(q) ? 1 : 0;
+        if (worklist_out) worklist_out[q] = c->last_W[seg].get(q) ? 1 : 0;
+    }
+    return QT_OK;
+}
+
+const char* qt_last_error(const qt_circuit* c) { return c ? c->err.c_str() : g_create_error.c_str(); }
+
+}  // extern "C"

@@ -1,0 +1,165 @@
+// qt_internal.h -- internal types shared by the host engine and the kernels
+// of libqtask.so.  Not part of the public ABI (include/qtask.h is).
+#pragma once
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "qtask.h"
+
+namespace qt {
+
+constexpr int kMaxQubits = 34;
+constexpr int kMaxTileHigh = 7;      // tile qubits above the contiguous low run
+constexpr int kThreads = 256;        // threads per fused-pass CTA
+
+// ------------------------------------------------------------------ ops --
+// A gate lowers to one primitive op; a fused pass is a sequence of ops applied
+// to one tile of amplitudes held in shared memory (see qt_kernels.cu).
+enum OpKind : int32_t {
+    OP_DENSE = 0,  // general complex 2x2 on target q0
+    OP_REAL = 1,   // real 2x2 on target q0
+    OP_DIAG = 2,   // diag(d0, d1) on q0 (q0 may lie outside the tile: uniform factor)
+    OP_PHASE = 3,  // multiply by f where every bit of cmask is 1 (Z S T CZ CP, fused phases)
+    OP_X = 4,      // exchange the pair on target q0
+    OP_ANTI = 5,   // [[0, m01], [m10, 0]] on target q0 (Y and fused permutation-phases)
+    OP_SWAP = 6,   // exchange amplitudes with (q0, q1) bits (1,0) and (0,1)
+};
+
+// Phase sub-kinds, chosen on the host so that exact factors cost no rounding.
+enum PhaseKind : int32_t { PH_GENERAL = 0, PH_NEG = 1, PH_POS_I = 2, PH_NEG_I = 3 };
+
+struct HostOp {
+    int32_t kind = OP_DENSE;
+    int32_t q0 = -1, q1 = -1;  // target qubits
+    uint64_t cmask = 0;        // qubits that must all be 1 (controls; for PHASE also the phase qubits)
+    double m[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    // DENSE/REAL: (m00, m01, m10, m11) as re,im pairs.  DIAG: d0 = m[0..1], d1 = m[2..3].
+    // PHASE: f = m[0..1].  ANTI: m01 = m[0..1], m10 = m[2..3].
+    int32_t ngates = 1;        // original gates folded into this op
+};
+
+// Public gate record as stored by the circuit.
+struct Gate {
+    qt_gate g;
+    qt_gate_id id;
+};
+
+struct Level {
+    std::vector<Gate> gates;  // kept in canonical order (ascending lowest qubit)
+};
+
+// ---------------------------------------------------------------- plans --
+struct Pass {
+    std::vector<HostOp> ops;
+    int32_t lt = 0;                 // tile low bits: amplitudes [0, 2^lt) are contiguous
+    int32_t nh = 0;                 // tile qubits at or above lt
+    int32_t h[kMaxTileHigh] = {0};  // those qubits, ascending
+    uint32_t M = 0;                 // partition-index bits spanned by the tile (coupling)
+    std::vector<uint32_t> supp_masks;  // partition q is touched iff (q & m) == m for some m
+    bool supp_all = false;
+    int32_t ngates = 0;
+    bool same_as(const Pass& o) const;
+};
+
+struct SegPlan {
+    int32_t first_level = 0, nlevels = 0;
+    std::vector<Pass> passes;
+};
+
+struct PlanParams {
+    int n = 0, p = 0;
+    int lt = 0;        // tile low bits
+    int nh_max = 0;    // tile qubits allowed at or above lt
+    bool fusion = true;
+};
+
+// Lower one public gate to primitive ops (A2: gate matrices and classification).
+bool lower_gate(const qt_gate& g, int n, std::vector<HostOp>* out, std::string* err);
+// Validate a gate against the circuit's qubit count.
+bool check_gate(const qt_gate& g, int n, std::string* err);
+uint64_t gate_qubit_mask(const qt_gate& g);
+
+// Plan one segment: canonical gate list -> fused passes (A3).
+SegPlan plan_segment(const std::vector<const qt_gate*>& gates, const PlanParams& pp);
+
+// Partition bitsets (A6).
+struct Bitset {
+    std::vector<uint64_t> w;
+    uint32_t nbits = 0;
+    void resize(uint32_t n) { nbits = n; w.assign((n + 63) / 64, 0); }
+    bool get(uint32_t i) const { return (w[i >> 6] >> (i & 63)) & 1; }
+    void set(uint32_t i) { w[i >> 6] |= uint64_t(1) << (i & 63); }
+    void fill() {
+        for (auto& x : w) x = ~uint64_t(0);
+        trim();
+    }
+    void trim() {
+        if (nbits & 63) w.back() &= (uint64_t(1) << (nbits & 63)) - 1;
+    }
+    bool any() const {
+        for (auto x : w)
+            if (x) return true;
+        return false;
+    }
+    bool all() const;
+    uint64_t count() const;
+    bool or_with(const Bitset& o);  // returns true if anything changed
+};
+
+Bitset pass_support(const Pass& ps, uint32_t nparts);
+// D := D u { q ^ m : q in D n supp, m in span(M) }
+void close_forward(Bitset* D, const Pass& ps, const Bitset& supp);
+// Smallest W containing F that is closed under every pass's coupling.
+void close_all(Bitset* W, const std::vector<Pass>& passes, const std::vector<Bitset>& supps);
+
+// ------------------------------------------------------- device encoding --
+// One op as the kernels read it (96 bytes).  Matrix entries are stored in the
+// arithmetic of the circuit's dtype: binary64 (QT_C128), binary32 (QT_C64) or
+// float-float (hi, lo) pairs (QT_C128_DF).
+struct DevOp {
+    int32_t kind;
+    int32_t b0;        // tile-local bit of target q0 (-1: q0 outside the tile; DIAG only)
+    int32_t b1;        // tile-local bit of q1 (SWAP) or the PhaseKind (PHASE)
+    int32_t gq;        // global qubit q0 (DIAG outside the tile)
+    uint64_t cm_glob;  // control bits outside the tile (global index positions)
+    int8_t fixpos[6];  // tile-local bits fixed by the op's index pattern, ascending
+    uint8_t nfix;      // number of fixed bits; the op visits 2^(tile bits - nfix) indices
+    uint8_t fixval;    // bit k = value of fixpos[k]
+    union {
+        double d[8];
+        float f[16];
+    } m;
+};
+static_assert(sizeof(DevOp) == 96, "DevOp layout");
+
+struct DevPass {
+    int32_t p;             // log2 partition size
+    int32_t lt;            // tile low bits
+    int32_t nh;            // tile high qubits
+    int32_t nins;          // tile high qubits below p (zeros inserted into the tile counter)
+    int32_t h[kMaxTileHigh];
+    int32_t ins[kMaxTileHigh];
+    int32_t tpg_log2;      // log2 tiles per partition group
+    int32_t nops;
+    uint32_t M;            // partition-index coupling mask
+    int32_t npart_log2;    // log2 number of partitions
+    int64_t op_offset;     // into the device op array
+};
+
+// Kernel launchers (qt_kernels.cu).  Return a cudaError_t as int.
+int launch_pass(int dtype, void* dst, const void* src, const DevPass& dp, const DevOp* ops,
+                const uint32_t* worklist, uint32_t ngroups, void* stream);
+int launch_copy_parts(int dtype, void* dst, const void* src, int p, const uint32_t* parts, uint32_t nparts,
+                      void* stream);
+int launch_init_zero_state(int dtype, void* state, uint64_t namps, void* stream);
+int launch_read_convert(int dtype, void* dst, const void* state, uint64_t first, uint64_t count, void* stream);
+int launch_norm(int dtype, const void* state, uint64_t namps, double* partials, int npartials, double* out_dev,
+                void* stream);
+int norm_partials_needed(uint64_t namps);
+size_t bytes_per_amp(int dtype);
+// Encode a host op for the device (matrix entries in the dtype's arithmetic).
+void encode_matrix(int dtype, const HostOp& op, DevOp* out);
+
+}  // namespace qt

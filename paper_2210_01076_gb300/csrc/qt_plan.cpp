@@ -1,0 +1,416 @@
+// qt_plan.cpp -- host side of the hot path: gate matrices and classification,
+// canonical order, tile fusion of a segment into passes, and the partition
+// support / coupling sets used by the dirty-partition tracker.
+//
+// qTask references: gate set, Table 1 and Section III-A; matrices, Section
+// II-A; non-superposition (swap and scale) versus superposition (matrix)
+// gates, Section III-C; parallel gates of a net may be ordered arbitrarily,
+// Section II-A; partitions of consecutive blocks, Section III-C; frontiers and
+// reachable partitions, Section III-E.
+#include <algorithm>
+#include <cmath>
+#include <complex>
+#include <cstring>
+
+#include "qt_internal.h"
+
+namespace qt {
+
+using cd = std::complex<double>;
+
+namespace {
+
+struct M2 {
+    cd a[4];  // row-major 2x2
+};
+
+M2 mul(const M2& x, const M2& y) {  // x * y
+    M2 r;
+    r.a[0] = x.a[0] * y.a[0] + x.a[1] * y.a[2];
+    r.a[1] = x.a[0] * y.a[1] + x.a[1] * y.a[3];
+    r.a[2] = x.a[2] * y.a[0] + x.a[3] * y.a[2];
+    r.a[3] = x.a[2] * y.a[1] + x.a[3] * y.a[3];
+    return r;
+}
+
+void put(double* m, int k, cd v) {
+    m[2 * k] = v.real();
+    m[2 * k + 1] = v.imag();
+}
+cd get(const double* m, int k) { return cd(m[2 * k], m[2 * k + 1]); }
+
+// Base 2x2 matrix of a one-target kind (for CNOT/CCX the X, for CZ the Z,
+// for CP the phase diag(1, e^{i theta})).
+bool base_matrix(const qt_gate& g, M2* U) {
+    const double t = g.theta[0];
+    const double c = std::cos(t / 2.0), s = std::sin(t / 2.0);
+    const double r2 = 1.0 / std::sqrt(2.0);
+    const cd I(0.0, 1.0);
+    cd* a = U->a;
+    a[0] = a[1] = a[2] = a[3] = 0.0;
+    switch (g.kind) {
+        case QT_H: a[0] = r2; a[1] = r2; a[2] = r2; a[3] = -r2; break;
+        case QT_X: case QT_CNOT: case QT_CCX: a[1] = 1.0; a[2] = 1.0; break;
+        case QT_Y: a[1] = -I; a[2] = I; break;
+        case QT_Z: case QT_CZ: a[0] = 1.0; a[3] = -1.0; break;
+        case QT_S: a[0] = 1.0; a[3] = I; break;
+        case QT_SDG: a[0] = 1.0; a[3] = -I; break;
+        case QT_T: a[0] = 1.0; a[3] = std::polar(1.0, M_PI / 4.0); break;
+        case QT_TDG: a[0] = 1.0; a[3] = std::polar(1.0, -M_PI / 4.0); break;
+        case QT_RX: a[0] = c; a[1] = -I * s; a[2] = -I * s; a[3] = c; break;
+        case QT_RY: a[0] = c; a[1] = -s; a[2] = s; a[3] = c; break;
+        case QT_RZ: a[0] = std::polar(1.0, -t / 2.0); a[3] = std::polar(1.0, t / 2.0); break;
+        case QT_U3: {
+            const double p = g.theta[1], l = g.theta[2];
+            a[0] = c;
+            a[1] = -std::polar(1.0, l) * s;
+            a[2] = std::polar(1.0, p) * s;
+            a[3] = std::polar(1.0, p + l) * c;
+            break;
+        }
+        case QT_CP: a[0] = 1.0; a[3] = std::polar(1.0, t); break;
+        default: return false;
+    }
+    return true;
+}
+
+// Classify a 2x2 by its exact structure (never by angle): diagonal,
+// anti-diagonal, real, or general.  The paper's swap/scale versus matrix
+// distinction (Section III-C) becomes the kernel specialisation.
+HostOp classify(const M2& U, int q, uint64_t cmask, int ngates) {
+    HostOp op;
+    op.q0 = q;
+    op.cmask = cmask;
+    op.ngates = ngates;
+    const cd *a = U.a;
+    if (a[1] == 0.0 && a[2] == 0.0) {
+        if (a[0] == 1.0) {
+            op.kind = OP_PHASE;
+            op.cmask |= uint64_t(1) << q;
+            put(op.m, 0, a[3]);
+        } else if (a[3] == 1.0) {
+            // diag(d0, 1): a phase on the 0 value of q; keep it a DIAG.
+            op.kind = OP_DIAG;
+            put(op.m, 0, a[0]);
+            put(op.m, 1, a[3]);
+        } else {
+            op.kind = OP_DIAG;
+            put(op.m, 0, a[0]);
+            put(op.m, 1, a[3]);
+        }
+        return op;
+    }
+    if (a[0] == 0.0 && a[3] == 0.0) {
+        if (a[1] == 1.0 && a[2] == 1.0) {
+            op.kind = OP_X;
+        } else {
+            op.kind = OP_ANTI;
+            put(op.m, 0, a[1]);
+            put(op.m, 1, a[2]);
+        }
+        return op;
+    }
+    bool real = true;
+    for (int k = 0; k < 4; ++k) real = real && a[k].imag() == 0.0;
+    op.kind = real ? OP_REAL : OP_DENSE;
+    for (int k = 0; k < 4; ++k) put(op.m, k, a[k]);
+    return op;
+}
+
+bool op_matrix(const HostOp& op, M2* U) {
+    cd* a = U->a;
+    a[0] = a[1] = a[2] = a[3] = 0.0;
+    switch (op.kind) {
+        case OP_DENSE: case OP_REAL:
+            for (int k = 0; k < 4; ++k) a[k] = get(op.m, k);
+            return true;
+        case OP_DIAG: a[0] = get(op.m, 0); a[3] = get(op.m, 1); return true;
+        case OP_PHASE: a[0] = 1.0; a[3] = get(op.m, 0); return true;
+        case OP_X: a[1] = 1.0; a[2] = 1.0; return true;
+        case OP_ANTI: a[1] = get(op.m, 0); a[2] = get(op.m, 1); return true;
+        default: return false;
+    }
+}
+
+// An op on one qubit with no other condition: mergeable into its neighbours.
+bool single_qubit(const HostOp& op) {
+    if (op.kind == OP_SWAP) return false;
+    if (op.kind == OP_PHASE) return op.cmask == (uint64_t(1) << op.q0);
+    return op.cmask == 0;
+}
+
+bool is_diagonal(const HostOp& op) { return op.kind == OP_DIAG || op.kind == OP_PHASE; }
+
+uint64_t op_qubits(const HostOp& op) {
+    uint64_t m = op.cmask;
+    if (op.q0 >= 0) m |= uint64_t(1) << op.q0;
+    if (op.q1 >= 0) m |= uint64_t(1) << op.q1;
+    return m;
+}
+
+int popcount64(uint64_t x) { return __builtin_popcountll(x); }
+
+}  // namespace
+
+uint64_t gate_qubit_mask(const qt_gate& g) {
+    uint64_t m = 0;
+    for (int k = 0; k < g.ntarget; ++k) m |= uint64_t(1) << g.target[k];
+    for (int k = 0; k < g.ncontrol; ++k) m |= uint64_t(1) << g.control[k];
+    return m;
+}
+
+bool check_gate(const qt_gate& g, int n, std::string* err) {
+    static const int nt[QT_NUM_KINDS] = {1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 2, 1, 1};
+    static const int nc[QT_NUM_KINDS] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 1, 1, 0, 2, 1};
+    if (g.kind < 0 || g.kind >= QT_NUM_KINDS) {
+        *err = "unknown gate kind " + std::to_string(g.kind);
+        return false;
+    }
+    if (g.ntarget != nt[g.kind] || g.ncontrol != nc[g.kind]) {
+        *err = "wrong number of targets/controls for kind " + std::to_string(g.kind);
+        return false;
+    }
+    uint64_t seen = 0;
+    for (int k = 0; k < g.ntarget + g.ncontrol; ++k) {
+        int q = k < g.ntarget ? g.target[k] : g.control[k - g.ntarget];
+        if (q < 0 || q >= n) {
+            *err = "qubit " + std::to_string(q) + " out of range";
+            return false;
+        }
+        if ((seen >> q) & 1) {
+            *err = "qubit " + std::to_string(q) + " used twice by one gate";
+            return false;
+        }
+        seen |= uint64_t(1) << q;
+    }
+    for (int k = 0; k < 3; ++k)
+        if (!std::isfinite(g.theta[k])) {
+            *err = "non-finite angle";
+            return false;
+        }
+    return true;
+}
+
+bool lower_gate(const qt_gate& g, int n, std::vector<HostOp>* out, std::string* err) {
+    if (!check_gate(g, n, err)) return false;
+    if (g.kind == QT_SWAP) {
+        HostOp op;
+        op.kind = OP_SWAP;
+        op.q0 = std::min(g.target[0], g.target[1]);
+        op.q1 = std::max(g.target[0], g.target[1]);
+        out->push_back(op);
+        return true;
+    }
+    M2 U;
+    if (!base_matrix(g, &U)) {
+        *err = "no matrix for kind";
+        return false;
+    }
+    uint64_t cmask = 0;
+    for (int k = 0; k < g.ncontrol; ++k) cmask |= uint64_t(1) << g.control[k];
+    out->push_back(classify(U, g.target[0], cmask, 1));
+    return true;
+}
+
+bool Pass::same_as(const Pass& o) const {
+    if (lt != o.lt || nh != o.nh || ops.size() != o.ops.size()) return false;
+    for (int k = 0; k < nh; ++k)
+        if (h[k] != o.h[k]) return false;
+    for (size_t i = 0; i < ops.size(); ++i) {
+        const HostOp &a = ops[i], &b = o.ops[i];
+        if (a.kind != b.kind || a.q0 != b.q0 || a.q1 != b.q1 || a.cmask != b.cmask || a.ngates != b.ngates)
+            return false;
+        if (std::memcmp(a.m, b.m, sizeof a.m) != 0) return false;
+    }
+    return true;
+}
+
+// Greedy tile fusion over a segment.  Gates come in canonical order (levels
+// in order, each level by ascending lowest qubit).  A pass collects, in order,
+// every gate that (a) does not depend on a gate left out of the pass (shares
+// no qubit with one), and (b) keeps the set of tile qubits at or above lt
+// within nh_max.  Diagonal ops and controls need no tile qubit: on a qubit
+// outside the tile they are uniform over the tile.  Consecutive one-qubit ops
+// on the same qubit are then multiplied into one 2x2 (FP64, on the host).
+SegPlan plan_segment(const std::vector<const qt_gate*>& gates, const PlanParams& pp) {
+    SegPlan sp;
+    struct Item {
+        std::vector<HostOp> ops;
+        uint64_t qubits;
+        uint64_t need;  // qubits >= lt that must be tile qubits
+    };
+    std::vector<Item> items;
+    items.reserve(gates.size());
+    for (const qt_gate* g : gates) {
+        Item it;
+        std::string err;
+        lower_gate(*g, pp.n, &it.ops, &err);
+        it.qubits = gate_qubit_mask(*g);
+        it.need = 0;
+        for (const HostOp& op : it.ops) {
+            if (is_diagonal(op)) continue;
+            if (op.q0 >= pp.lt) it.need |= uint64_t(1) << op.q0;
+            if (op.q1 >= pp.lt) it.need |= uint64_t(1) << op.q1;
+        }
+        items.push_back(std::move(it));
+    }
+    std::vector<char> done(items.size(), 0);
+    size_t ndone = 0;
+    const uint32_t nparts_bits = pp.n - pp.p;
+    while (ndone < items.size()) {
+        Pass ps;
+        uint64_t H = 0, blocked = 0;
+        std::vector<HostOp> ops;
+        for (size_t i = 0; i < items.size(); ++i) {
+            if (done[i]) continue;
+            const Item& it = items[i];
+            if (it.qubits & blocked) {
+                blocked |= it.qubits;
+                continue;
+            }
+            uint64_t nH = H | it.need;
+            bool fits = popcount64(nH) <= pp.nh_max;
+            if (!pp.fusion && !ops.empty()) fits = false;
+            if (!fits) {
+                blocked |= it.qubits;
+                continue;
+            }
+            H = nH;
+            for (const HostOp& op : it.ops) ops.push_back(op);
+            ps.ngates += 1;
+            done[i] = 1;
+            ++ndone;
+        }
+        // Merge consecutive one-qubit ops on the same qubit.
+        std::vector<HostOp> merged;
+        std::vector<int> last(pp.n, -1);  // index into merged of the last op touching q
+        for (const HostOp& op : ops) {
+            uint64_t qs = op_qubits(op);
+            if (single_qubit(op) && last[op.q0] >= 0 && single_qubit(merged[last[op.q0]]) &&
+                merged[last[op.q0]].q0 == op.q0) {
+                HostOp& prev = merged[last[op.q0]];
+                M2 a, b;
+                op_matrix(prev, &a);
+                op_matrix(op, &b);
+                prev = classify(mul(b, a), op.q0, 0, prev.ngates + op.ngates);
+                continue;
+            }
+            merged.push_back(op);
+            for (int q = 0; q < pp.n; ++q)
+                if ((qs >> q) & 1) last[q] = int(merged.size()) - 1;
+        }
+        // Drop exact identities left by merging.
+        for (const HostOp& op : merged) {
+            bool ident = false;
+            if (op.kind == OP_PHASE && op.m[0] == 1.0 && op.m[1] == 0.0) ident = true;
+            if (op.kind == OP_DIAG && op.m[0] == 1.0 && op.m[1] == 0.0 && op.m[2] == 1.0 && op.m[3] == 0.0)
+                ident = true;
+            if (!ident) ps.ops.push_back(op);
+        }
+        ps.lt = pp.lt;
+        ps.nh = 0;
+        for (int q = pp.lt; q < pp.n; ++q)
+            if ((H >> q) & 1) ps.h[ps.nh++] = q;
+        ps.M = 0;
+        for (int k = 0; k < ps.nh; ++k)
+            if (ps.h[k] >= pp.p) ps.M |= uint32_t(1) << (ps.h[k] - pp.p);
+        // Support: partitions where some op can act -- its partition-level
+        // conditions (controls and phase qubits at or above p) all hold.
+        ps.supp_all = false;
+        for (const HostOp& op : ps.ops) {
+            uint32_t pm = nparts_bits ? uint32_t(op.cmask >> pp.p) : 0;
+            if (pm == 0) ps.supp_all = true;
+            ps.supp_masks.push_back(pm);
+        }
+        if (ps.ops.empty()) ps.supp_all = false;  // a pass reduced to nothing touches nothing
+        if (ps.ngates > 0) sp.passes.push_back(std::move(ps));
+    }
+    return sp;
+}
+
+// ------------------------------------------------------------ bitsets ---
+
+bool Bitset::all() const {
+    for (uint32_t i = 0; i + 1 < w.size(); ++i)
+        if (w[i] != ~uint64_t(0)) return false;
+    if (w.empty()) return true;
+    uint64_t lastmask = (nbits & 63) ? (uint64_t(1) << (nbits & 63)) - 1 : ~uint64_t(0);
+    return w.back() == lastmask;
+}
+
+uint64_t Bitset::count() const {
+    uint64_t c = 0;
+    for (auto x : w) c += __builtin_popcountll(x);
+    return c;
+}
+
+bool Bitset::or_with(const Bitset& o) {
+    bool ch = false;
+    for (size_t i = 0; i < w.size(); ++i) {
+        uint64_t nw = w[i] | o.w[i];
+        ch = ch || nw != w[i];
+        w[i] = nw;
+    }
+    return ch;
+}
+
+Bitset pass_support(const Pass& ps, uint32_t nparts) {
+    Bitset s;
+    s.resize(nparts);
+    if (ps.supp_all) {
+        s.fill();
+        return s;
+    }
+    for (uint32_t pm : ps.supp_masks)
+        for (uint32_t q = 0; q < nparts; ++q)
+            if ((q & pm) == pm) s.set(q);
+    return s;
+}
+
+namespace {
+// Mark every member of each coupling group that meets T.
+bool mark_groups(Bitset* D, const Bitset& T, uint32_t M) {
+    bool changed = false;
+    for (size_t wi = 0; wi < T.w.size(); ++wi) {
+        uint64_t word = T.w[wi];
+        while (word) {
+            int b = __builtin_ctzll(word);
+            word &= word - 1;
+            uint32_t q = uint32_t(wi * 64 + b);
+            uint32_t g = q & ~M;
+            uint32_t m = 0;
+            do {
+                uint32_t r = g | m;
+                if (!D->get(r)) {
+                    D->set(r);
+                    changed = true;
+                }
+                m = (m - M) & M;
+            } while (m != 0);
+        }
+    }
+    return changed;
+}
+}  // namespace
+
+void close_forward(Bitset* D, const Pass& ps, const Bitset& supp) {
+    if (ps.M == 0 || D->all()) return;
+    Bitset T = *D;
+    for (size_t i = 0; i < T.w.size(); ++i) T.w[i] &= supp.w[i];
+    mark_groups(D, T, ps.M);
+}
+
+void close_all(Bitset* W, const std::vector<Pass>& passes, const std::vector<Bitset>& supps) {
+    bool changed = true;
+    while (changed && !W->all()) {
+        changed = false;
+        for (size_t i = 0; i < passes.size(); ++i) {
+            if (passes[i].M == 0) continue;
+            Bitset T = *W;
+            for (size_t k = 0; k < T.w.size(); ++k) T.w[k] &= supps[i].w[k];
+            changed = mark_groups(W, T, passes[i].M) || changed;
+        }
+    }
+}
+
+}  // namespace qt
