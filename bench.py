@@ -172,6 +172,9 @@ def run_ours(args):
     c = B.Circuit(N_QUBITS, "c128df", LOG2_PART)
     c.set_stream(stream.cuda_stream)
     c.set_option("ckpt_interval", CKPT)
+    for kv in args.option:
+        k, v = kv.split("=")
+        c.set_option(k, int(v))
     ids = c.load_levels(levels)
     h2id, k = {}, 0
     for lv in ids:
@@ -239,7 +242,7 @@ def run_ours(args):
     host_state = torch.empty((1 << N_QUBITS,), dtype=torch.complex128).pin_memory()
     host_np = host_state.numpy()
     e2e_amp, e2e_h2d = 0, 0
-    e2e_rounds = min(args.steps, max(1, len(edits) - ri))
+    e2e_rounds = 0 if args.no_e2e else min(args.steps, max(1, len(edits) - ri))
     barrier()
     te0 = time.perf_counter()
     for _ in range(e2e_rounds):
@@ -251,13 +254,13 @@ def run_ours(args):
         ri += 1
     barrier()
     te = time.perf_counter() - te0
-    e2e_val = e2e_amp / te
+    e2e_val = e2e_amp / te if e2e_rounds else None
     if world > 1:
         t = torch.tensor([te], device=dev, dtype=torch.float64)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         a = torch.tensor([float(e2e_amp)], device=dev, dtype=torch.float64)
         dist.all_reduce(a)
-        e2e_val = float(a.item()) / float(t.item())
+        e2e_val = float(a.item()) / float(t.item()) if e2e_rounds else None
 
     # ---- accuracy of the final state against the oracle (rank 0; the
     # oracle's state after the same rounds), and the norm
@@ -317,7 +320,7 @@ def run_ours(args):
                          "traffic": traffic_per_launch, "kernel": "k_pass<ArDF> (fused tile pass)",
                          "bytes_per_unit": "32 B per amplitude per pass (read + write of 16 B)",
                          "kernel_ms_total": kern_ms, "kernel_launches": kern_launches},
-            "e2e": {"value": e2e_val, "unit": "amp-updates/s", "h2d_bytes_per_step": e2e_h2d / e2e_rounds,
+            "e2e": {"value": e2e_val, "unit": "amp-updates/s", "h2d_bytes_per_step": e2e_h2d / max(e2e_rounds, 1),
                     "d2h_bytes_per_step": (1 << N_QUBITS) * 16, "steps": e2e_rounds,
                     "note": "edits in, qt_update_state, whole state read to pinned host memory, each step"},
             "clocks": clocks,
@@ -401,7 +404,13 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-oracle-check", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg (profiling runs)")
+    ap.add_argument("--n-qubits", type=int, default=N_QUBITS, help="smaller cases for profiling only")
+    ap.add_argument("--ckpt", type=int, default=CKPT, help="levels per checkpoint segment")
+    ap.add_argument("--option", action="append", default=[], help="extra qt_set_option key=value")
     args = ap.parse_args()
+    global N_QUBITS, CKPT
+    N_QUBITS, CKPT = args.n_qubits, args.ckpt
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3
     if args.impl == "reference":

@@ -104,7 +104,8 @@ typedef struct {
     int64_t partition_passes_total;     /* sum over all passes of all partitions */
     int64_t partition_passes_run;       /* sum over launched passes of partitions processed */
     double clean_fraction;       /* 1 - run / total partition-passes */
-    uint64_t amp_updates;        /* sum over gates of amplitudes processed (full run: gates x 2^n) */
+    uint64_t amp_updates;        /* sum over gates of the amplitudes recomputed in the gate's segment
+                                    (a full run: gates x 2^n) */
     uint64_t hbm_bytes;          /* algorithmic bytes: 2 x bytes/amp x amplitudes, per pass */
     double host_ms;              /* wall time of the call */
     double gpu_ms;               /* device time of the call's stream work (CUDA events), -1 if not timed */
@@ -175,6 +176,8 @@ qt_status qt_norm(const qt_circuit* c, double* out);
  *   "tile_high"      max qubits at or above the tile's low bits per pass (0..7)
  *   "mem_limit"      device-memory budget in bytes for state + checkpoints (0 = none)
  *   "kernel_timing"  1: time every fused-pass kernel with CUDA events (stats)
+ *   "reg_kernel"     1: register-resident pass kernel for tiles of 2^7 amplitudes or more
+ *                    (default); 0: shared-memory pass kernel for every tile
  *   "dry_run"        1: qt_update_state plans and tracks but launches nothing and
  *                    allocates nothing (host-logic testing); the device state is
  *                    marked stale and the next real update runs in full.

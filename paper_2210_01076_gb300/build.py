@@ -82,4 +82,4 @@ def build(force: bool = False, verbose: bool = False, extra_nvcc=()) -> str:
 
 
 if __name__ == "__main__":
-    print(build(force="--force" in sys.argv, verbose=True))
+    print(build(force="--force" in sys.argv, verbose="--verbose" in sys.argv))

@@ -64,6 +64,7 @@ struct qt_circuit {
     int64_t mem_limit = 0;
     bool kernel_timing = false;
     bool dry_run = false;
+    bool reg_kernel = true;
 
     // committed plan (matches the slabs when device_valid)
     bool have_plan = false;
@@ -279,14 +280,18 @@ DevOp encode_op(int dtype, const Pass& ps, const HostOp& op) {
             break;
         case OP_PHASE: {
             const double re = op.m[0], im = op.m[1];
-            d.b1 = PH_GENERAL;
-            if (re == -1.0 && im == 0.0) d.b1 = PH_NEG;
-            else if (re == 0.0 && im == 1.0) d.b1 = PH_POS_I;
-            else if (re == 0.0 && im == -1.0) d.b1 = PH_NEG_I;
+            d.sub = PH_GENERAL;
+            if (re == -1.0 && im == 0.0) d.sub = PH_NEG;
+            else if (re == 0.0 && im == 1.0) d.sub = PH_POS_I;
+            else if (re == 0.0 && im == -1.0) d.sub = PH_NEG_I;
             break;
         }
         default: break;
     }
+    // tile-local control mask (the register-layout planner splits it)
+    d.cm_thr = 0;
+    for (int q = 0; q < 64; ++q)
+        if (((op.cmask & tile_mask) >> q) & 1) d.cm_thr |= 1u << loc(q);
     std::sort(fixed.begin(), fixed.end());
     d.nfix = uint8_t(fixed.size());
     d.fixval = 0;
@@ -351,6 +356,7 @@ qt_status do_update(qt_circuit* c, int force_full, qt_update_stats* stats) {
     std::vector<DevOp> hops;
     std::vector<uint32_t> hwl;
     std::vector<Bitset> lastF(S), lastW(S);
+    uint64_t seg_amp_updates = 0;
     Bitset dirty_in;
     dirty_in.resize(nparts);
     const int old_S = c->have_plan ? int(c->plans.size()) : 0;
@@ -393,6 +399,12 @@ qt_status do_update(qt_circuit* c, int force_full, qt_update_stats* stats) {
         dirty_in = F;
         if (!W.any()) continue;
         st.segments_run += 1;
+        {
+            // every gate of the segment is (re)applied to the recomputed partitions W
+            int64_t seg_gates = 0;
+            for (const Pass& ps : np.passes) seg_gates += ps.ngates;
+            seg_amp_updates += W.count() * (uint64_t(1) << c->p) * uint64_t(seg_gates);
+        }
         if (np.passes.empty()) {
             Launch ln{};
             ln.kind = 1;
@@ -453,7 +465,12 @@ qt_status do_update(qt_circuit* c, int force_full, qt_update_stats* stats) {
             dp.M = ps.M;
             dp.npart_log2 = c->n - c->p;
             dp.op_offset = int64_t(hops.size());
-            for (const HostOp& o : ps.ops) hops.push_back(encode_op(c->dtype, ps, o));
+            std::vector<DevOp> pops;
+            pops.reserve(ps.ops.size());
+            for (const HostOp& o : ps.ops) pops.push_back(encode_op(c->dtype, ps, o));
+            if (c->reg_kernel) plan_register_layout(&dp, &pops);
+            dp.nops = int32_t(pops.size());
+            hops.insert(hops.end(), pops.begin(), pops.end());
             launches.push_back(ln);
         }
     }
@@ -472,10 +489,10 @@ qt_status do_update(qt_circuit* c, int force_full, qt_update_stats* stats) {
         if (ln.kind == 0) {
             st.passes_run += 1;
             st.partition_passes_run += int64_t(ln.parts_processed);
-            st.amp_updates += ln.parts_processed * part_amps * uint64_t(ln.ngates);
         }
         st.hbm_bytes += 2 * bpa * ln.parts_processed * part_amps;
     }
+    st.amp_updates = seg_amp_updates;
     st.clean_fraction =
         st.partition_passes_total ? 1.0 - double(st.partition_passes_run) / double(st.partition_passes_total) : 0.0;
 
@@ -840,6 +857,8 @@ qt_status qt_set_option(qt_circuit* c, const char* key, int64_t value) {
         c->mem_limit = value;
     } else if (k == "kernel_timing") {
         c->kernel_timing = value != 0;
+    } else if (k == "reg_kernel") {
+        c->reg_kernel = value != 0;
     } else if (k == "dry_run") {
         c->dry_run = value != 0;
     } else {

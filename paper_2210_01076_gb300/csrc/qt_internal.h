@@ -118,21 +118,44 @@ void close_all(Bitset* W, const std::vector<Pass>& passes, const std::vector<Bit
 // One op as the kernels read it (96 bytes).  Matrix entries are stored in the
 // arithmetic of the circuit's dtype: binary64 (QT_C128), binary32 (QT_C64) or
 // float-float (hi, lo) pairs (QT_C128_DF).
+//
+// Two kernels read it.  The shared-memory kernel (small tiles) walks the
+// op's index pattern (fixpos/fixval).  The register kernel (tiles of 2^7 and
+// more) keeps each thread's amplitudes in registers: tile bits 0-4 are the
+// lane bits, the other tile bits are split between register-index bits and
+// warp bits by the current layout; OP_PERM ops change the layout through
+// shared memory so that every target is a lane or register bit when its op
+// runs.  Roles: 0..7 = register-index bit, kRoleLane + b = lane bit b,
+// kRoleThread + t = tile bit t held by the lane or warp index (DIAG only),
+// kRoleNone = outside the tile.
+constexpr int8_t kRoleLane = 32;
+constexpr int8_t kRoleThread = 64;
+constexpr int8_t kRoleNone = -1;
+
+enum : int32_t { OP_PERM = 7 };  // register-kernel layout change
+
 struct DevOp {
     int32_t kind;
     int32_t b0;        // tile-local bit of target q0 (-1: q0 outside the tile; DIAG only)
-    int32_t b1;        // tile-local bit of q1 (SWAP) or the PhaseKind (PHASE)
+    int32_t b1;        // tile-local bit of q1 (SWAP)
     int32_t gq;        // global qubit q0 (DIAG outside the tile)
     uint64_t cm_glob;  // control bits outside the tile (global index positions)
     int8_t fixpos[6];  // tile-local bits fixed by the op's index pattern, ascending
     uint8_t nfix;      // number of fixed bits; the op visits 2^(tile bits - nfix) indices
     uint8_t fixval;    // bit k = value of fixpos[k]
+    uint32_t cm_thr;   // register kernel: control bits among lane and warp tile bits
+    uint16_t cm_reg;   // register kernel: control bits among register-index bits
+    int8_t role0, role1;  // register kernel: roles of q0 and q1
+    int8_t sub;        // PhaseKind (PHASE)
+    int8_t nreg, nwarp;  // OP_PERM: register bits and warp bits of the new layout
+    int8_t perm[8];    // OP_PERM: tile bit of register bit k (k < nreg), then of warp bit w
+    int8_t pad[9];
     union {
         double d[8];
         float f[16];
     } m;
 };
-static_assert(sizeof(DevOp) == 96, "DevOp layout");
+static_assert(sizeof(DevOp) == 128, "DevOp layout");
 
 struct DevPass {
     int32_t p;             // log2 partition size
@@ -146,11 +169,20 @@ struct DevPass {
     uint32_t M;            // partition-index coupling mask
     int32_t npart_log2;    // log2 number of partitions
     int64_t op_offset;     // into the device op array
+    int32_t reg_kernel;    // 1: register kernel with the initial layout below
+    int32_t nreg, nwarp;   // register-index bits and warp bits (lane bits = 5)
+    int32_t layout[8];     // tile bit of register bit k (k < nreg), then of warp bit w
 };
+
+// Register-kernel layout planning for one pass (host): fills the initial
+// layout of dp and rewrites the ops' roles, inserting OP_PERM where needed.
+void plan_register_layout(DevPass* dp, std::vector<DevOp>* ops);
 
 // Kernel launchers (qt_kernels.cu).  Return a cudaError_t as int.
 int launch_pass(int dtype, void* dst, const void* src, const DevPass& dp, const DevOp* ops,
                 const uint32_t* worklist, uint32_t ngroups, void* stream);
+int launch_pass_reg(int dtype, void* dst, const void* src, const DevPass& dp, const DevOp* ops,
+                    const uint32_t* worklist, uint32_t ngroups, void* stream);
 int launch_copy_parts(int dtype, void* dst, const void* src, int p, const uint32_t* parts, uint32_t nparts,
                       void* stream);
 int launch_init_zero_state(int dtype, void* state, uint64_t namps, void* stream);

@@ -32,145 +32,10 @@
 
 #include <cstdint>
 
+#include "qt_arith.cuh"
 #include "qt_internal.h"
 
 namespace qt {
-
-// ------------------------------------------------------------ float-float --
-struct df {
-    float hi, lo;
-};
-
-__device__ __forceinline__ df two_sum(float a, float b) {
-    float s = __fadd_rn(a, b);
-    float bb = __fsub_rn(s, a);
-    float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
-    return {s, e};
-}
-
-__device__ __forceinline__ df fast_two_sum(float a, float b) {
-    float s = __fadd_rn(a, b);
-    float e = __fsub_rn(b, __fsub_rn(s, a));
-    return {s, e};
-}
-
-__device__ __forceinline__ df dneg(df a) { return {-a.hi, -a.lo}; }
-
-// sum_k a_k * b_k for K float-float pairs.  Each product's leading term is
-// split exactly by an FMA; the leading terms are summed with two_sum and all
-// residuals gathered in one float before a final renormalisation.
-template <int K>
-__device__ __forceinline__ df df_dot(const df (&a)[K], const df (&b)[K]) {
-    float p = __fmul_rn(a[0].hi, b[0].hi);
-    float err = __fmaf_rn(a[0].hi, b[0].hi, -p);
-    err = __fmaf_rn(a[0].hi, b[0].lo, err);
-    err = __fmaf_rn(a[0].lo, b[0].hi, err);
-    float s = p;
-#pragma unroll
-    for (int k = 1; k < K; ++k) {
-        float pk = __fmul_rn(a[k].hi, b[k].hi);
-        float ek = __fmaf_rn(a[k].hi, b[k].hi, -pk);
-        ek = __fmaf_rn(a[k].hi, b[k].lo, ek);
-        ek = __fmaf_rn(a[k].lo, b[k].hi, ek);
-        df t = two_sum(s, pk);
-        s = t.hi;
-        err = __fadd_rn(err, __fadd_rn(t.lo, ek));
-    }
-    return fast_two_sum(s, err);
-}
-
-// ----------------------------------------------------------------- policies
-struct ArF64 {
-    using amp_t = double2;
-    struct cx {
-        double re, im;
-    };
-    static __device__ __forceinline__ cx ld(amp_t a) { return {a.x, a.y}; }
-    static __device__ __forceinline__ amp_t st(cx v) { return make_double2(v.re, v.im); }
-    static __device__ __forceinline__ cx mat(const DevOp& op, int k) { return {op.m.d[2 * k], op.m.d[2 * k + 1]}; }
-    // u0 * x0 + u1 * x1
-    static __device__ __forceinline__ cx lin2(cx u0, cx x0, cx u1, cx x1) {
-        cx r;
-        r.re = __fma_rn(u0.re, x0.re, __fma_rn(-u0.im, x0.im, __fma_rn(u1.re, x1.re, __dmul_rn(-u1.im, x1.im))));
-        r.im = __fma_rn(u0.re, x0.im, __fma_rn(u0.im, x0.re, __fma_rn(u1.re, x1.im, __dmul_rn(u1.im, x1.re))));
-        return r;
-    }
-    static __device__ __forceinline__ cx lin2r(cx u0, cx x0, cx u1, cx x1) {  // real u
-        cx r;
-        r.re = __fma_rn(u0.re, x0.re, __dmul_rn(u1.re, x1.re));
-        r.im = __fma_rn(u0.re, x0.im, __dmul_rn(u1.re, x1.im));
-        return r;
-    }
-    static __device__ __forceinline__ cx mul(cx a, cx b) {
-        return {__fma_rn(a.re, b.re, __dmul_rn(-a.im, b.im)), __fma_rn(a.re, b.im, __dmul_rn(a.im, b.re))};
-    }
-    static __device__ __forceinline__ cx neg(cx a) { return {-a.re, -a.im}; }
-    static __device__ __forceinline__ cx mul_i(cx a) { return {-a.im, a.re}; }
-    static __device__ __forceinline__ cx mul_negi(cx a) { return {a.im, -a.re}; }
-};
-
-struct ArF32 {
-    using amp_t = float2;
-    struct cx {
-        float re, im;
-    };
-    static __device__ __forceinline__ cx ld(amp_t a) { return {a.x, a.y}; }
-    static __device__ __forceinline__ amp_t st(cx v) { return make_float2(v.re, v.im); }
-    static __device__ __forceinline__ cx mat(const DevOp& op, int k) { return {op.m.f[2 * k], op.m.f[2 * k + 1]}; }
-    static __device__ __forceinline__ cx lin2(cx u0, cx x0, cx u1, cx x1) {
-        cx r;
-        r.re = __fmaf_rn(u0.re, x0.re, __fmaf_rn(-u0.im, x0.im, __fmaf_rn(u1.re, x1.re, __fmul_rn(-u1.im, x1.im))));
-        r.im = __fmaf_rn(u0.re, x0.im, __fmaf_rn(u0.im, x0.re, __fmaf_rn(u1.re, x1.im, __fmul_rn(u1.im, x1.re))));
-        return r;
-    }
-    static __device__ __forceinline__ cx lin2r(cx u0, cx x0, cx u1, cx x1) {
-        cx r;
-        r.re = __fmaf_rn(u0.re, x0.re, __fmul_rn(u1.re, x1.re));
-        r.im = __fmaf_rn(u0.re, x0.im, __fmul_rn(u1.re, x1.im));
-        return r;
-    }
-    static __device__ __forceinline__ cx mul(cx a, cx b) {
-        return {__fmaf_rn(a.re, b.re, __fmul_rn(-a.im, b.im)), __fmaf_rn(a.re, b.im, __fmul_rn(a.im, b.re))};
-    }
-    static __device__ __forceinline__ cx neg(cx a) { return {-a.re, -a.im}; }
-    static __device__ __forceinline__ cx mul_i(cx a) { return {-a.im, a.re}; }
-    static __device__ __forceinline__ cx mul_negi(cx a) { return {a.im, -a.re}; }
-};
-
-struct ArDF {
-    using amp_t = float4;  // (re.hi, re.lo, im.hi, im.lo)
-    struct cx {
-        df re, im;
-    };
-    static __device__ __forceinline__ cx ld(amp_t a) { return {{a.x, a.y}, {a.z, a.w}}; }
-    static __device__ __forceinline__ amp_t st(cx v) { return make_float4(v.re.hi, v.re.lo, v.im.hi, v.im.lo); }
-    static __device__ __forceinline__ cx mat(const DevOp& op, int k) {
-        return {{op.m.f[4 * k], op.m.f[4 * k + 1]}, {op.m.f[4 * k + 2], op.m.f[4 * k + 3]}};
-    }
-    static __device__ __forceinline__ cx lin2(cx u0, cx x0, cx u1, cx x1) {
-        const df ar[4] = {u0.re, dneg(u0.im), u1.re, dneg(u1.im)};
-        const df br[4] = {x0.re, x0.im, x1.re, x1.im};
-        const df ai[4] = {u0.re, u0.im, u1.re, u1.im};
-        const df bi[4] = {x0.im, x0.re, x1.im, x1.re};
-        return {df_dot<4>(ar, br), df_dot<4>(ai, bi)};
-    }
-    static __device__ __forceinline__ cx lin2r(cx u0, cx x0, cx u1, cx x1) {
-        const df a[2] = {u0.re, u1.re};
-        const df br[2] = {x0.re, x1.re};
-        const df bi[2] = {x0.im, x1.im};
-        return {df_dot<2>(a, br), df_dot<2>(a, bi)};
-    }
-    static __device__ __forceinline__ cx mul(cx a, cx b) {
-        const df ar[2] = {a.re, dneg(a.im)};
-        const df br[2] = {b.re, b.im};
-        const df ai[2] = {a.re, a.im};
-        const df bi[2] = {b.im, b.re};
-        return {df_dot<2>(ar, br), df_dot<2>(ai, bi)};
-    }
-    static __device__ __forceinline__ cx neg(cx a) { return {dneg(a.re), dneg(a.im)}; }
-    static __device__ __forceinline__ cx mul_i(cx a) { return {dneg(a.im), a.re}; }
-    static __device__ __forceinline__ cx mul_negi(cx a) { return {a.im, dneg(a.re)}; }
-};
 
 // ---------------------------------------------------------------- helpers --
 // Expand a counter into a tile index by inserting the op's fixed bits.
@@ -262,7 +127,7 @@ __device__ __forceinline__ void apply_op(typename A::amp_t* tile, uint32_t tb, c
         }
         case OP_PHASE: {
             const cx f = A::mat(op, 0);
-            const int sub = op.b1;
+            const int sub = op.sub;
             for (uint32_t k = threadIdx.x; k < iters; k += blockDim.x) {
                 const uint32_t i = expand_fixed(k, op);
                 const cx x = A::ld(tile[i]);
@@ -357,6 +222,7 @@ int launch_pass_t(void* dst, const void* src, const DevPass& dp, const DevOp* op
 
 int launch_pass(int dtype, void* dst, const void* src, const DevPass& dp, const DevOp* ops, const uint32_t* worklist,
                 uint32_t ngroups, void* stream) {
+    if (dp.reg_kernel) return launch_pass_reg(dtype, dst, src, dp, ops, worklist, ngroups, stream);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     switch (dtype) {
         case QT_C128: return launch_pass_t<ArF64>(dst, src, dp, ops, worklist, ngroups, st);

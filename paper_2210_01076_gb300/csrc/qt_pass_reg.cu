@@ -1,0 +1,402 @@
+// qt_pass_reg.cu -- register-resident fused pass (tiles of 2^7..2^13 amplitudes).
+//
+// Same contract as the shared-memory pass of qt_kernels.cu (one CTA per tile
+// of the worklist's partition groups, one HBM read and one write per
+// amplitude per pass), but every thread keeps its 2^RB amplitudes of the tile
+// in registers for the whole pass:
+//
+//   tile index j = lane bits (j bits 0..4, the lane id) | register bits
+//                  (register index r) | warp bits (warp id)
+//
+// so a warp always holds 32 consecutive amplitudes (coalesced loads and
+// stores, conflict-free shared memory).  An op whose target is a register bit
+// pairs registers of the same thread; a target that is a lane bit exchanges
+// the partner amplitude with a warp shuffle (the low-stride qubits); the host
+// inserts an OP_PERM before an op whose target is a warp bit, which rewrites
+// the layout through shared memory (one read and one write of the tile) so
+// that the target becomes a register bit.  Diagonal ops, phases and controls
+// need no particular layout: each thread knows the index of every amplitude
+// it holds.
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "qt_arith.cuh"
+#include "qt_internal.h"
+
+namespace qt {
+
+template <int V>
+struct IC {
+    static constexpr int value = V;
+};
+
+// Call f(IC<k>) for a runtime k in [0, RB).
+template <int RB, class F>
+__device__ __forceinline__ void dispatch_k(int k, F&& f) {
+    if (k == 0) {
+        f(IC<0>{});
+    } else if (k == 1) {
+        f(IC<1>{});
+    } else if constexpr (RB > 2) {
+        if (k == 2) {
+            f(IC<2>{});
+        } else if constexpr (RB > 3) {
+            if (k == 3) {
+                f(IC<3>{});
+            } else if constexpr (RB > 4) {
+                if (k == 4) f(IC<4>{});
+            }
+        }
+    }
+}
+
+template <class A, int RB>
+struct RegOps {
+    using cx = typename A::cx;
+    static constexpr int R = 1 << RB;
+
+    // one-target ops on register bit K: (x[r], x[r | 2^K]) for r with bit K = 0
+    template <int K>
+    static __device__ __forceinline__ void pair_reg(int kind, cx (&x)[R], const DevOp* op, bool thr_ok,
+                                                    uint32_t cmr) {
+        if (kind == OP_DENSE || kind == OP_REAL) {
+            const cx u00 = A::matp(op, 0), u01 = A::matp(op, 1), u10 = A::matp(op, 2), u11 = A::matp(op, 3);
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                if (r & (1 << K)) continue;
+                const int r1 = r | (1 << K);
+                if (!(thr_ok && (uint32_t(r) & cmr) == cmr)) continue;
+                const cx a = x[r], b = x[r1];
+                if (kind == OP_DENSE) {
+                    x[r] = A::lin2(u00, a, u01, b);
+                    x[r1] = A::lin2(u10, a, u11, b);
+                } else {
+                    x[r] = A::lin2r(u00, a, u01, b);
+                    x[r1] = A::lin2r(u10, a, u11, b);
+                }
+            }
+        } else if (kind == OP_X) {
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                if (r & (1 << K)) continue;
+                const int r1 = r | (1 << K);
+                if (!(thr_ok && (uint32_t(r) & cmr) == cmr)) continue;
+                const cx a = x[r];
+                x[r] = x[r1];
+                x[r1] = a;
+            }
+        } else {  // OP_ANTI
+            const cx m01 = A::matp(op, 0), m10 = A::matp(op, 1);
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                if (r & (1 << K)) continue;
+                const int r1 = r | (1 << K);
+                if (!(thr_ok && (uint32_t(r) & cmr) == cmr)) continue;
+                const cx a = x[r], b = x[r1];
+                x[r] = A::mul(m01, b);
+                x[r1] = A::mul(m10, a);
+            }
+        }
+    }
+
+    // one-target ops on lane bit b: the partner amplitude comes from lane ^ 2^b
+    static __device__ __forceinline__ void pair_lane(int kind, cx (&x)[R], const DevOp* op, int b, uint32_t lane,
+                                                     bool thr_ok, uint32_t cmr) {
+        const int mask = 1 << b;
+        const bool hi = (lane >> b) & 1u;
+        if (kind == OP_DENSE || kind == OP_REAL) {
+            // the bit-0 output is u00 a0 + u01 a1, the bit-1 output u10 a0 + u11 a1
+            const cx c0 = A::sel(hi, A::matp(op, 2), A::matp(op, 0));
+            const cx c1 = A::sel(hi, A::matp(op, 3), A::matp(op, 1));
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                const cx p = A::shfl(x[r], mask);
+                const cx a0 = A::sel(hi, p, x[r]), a1 = A::sel(hi, x[r], p);
+                const cx y = (kind == OP_DENSE) ? A::lin2(c0, a0, c1, a1) : A::lin2r(c0, a0, c1, a1);
+                if (thr_ok && (uint32_t(r) & cmr) == cmr) x[r] = y;
+            }
+        } else if (kind == OP_X) {
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                const cx p = A::shfl(x[r], mask);
+                if (thr_ok && (uint32_t(r) & cmr) == cmr) x[r] = p;
+            }
+        } else {  // OP_ANTI: bit-0 output m01 a1, bit-1 output m10 a0
+            const cx c = A::sel(hi, A::matp(op, 1), A::matp(op, 0));
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                const cx p = A::shfl(x[r], mask);
+                const cx y = A::mul(c, p);
+                if (thr_ok && (uint32_t(r) & cmr) == cmr) x[r] = y;
+            }
+        }
+    }
+
+    // SWAP on register bits K0 < K1: exchange (bit K0, bit K1) = (1,0) and (0,1)
+    template <int K0, int K1>
+    static __device__ __forceinline__ void swap_rr(cx (&x)[R], bool thr_ok, uint32_t cmr) {
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            if (!((r >> K0) & 1) || ((r >> K1) & 1)) continue;
+            const int r2 = r ^ ((1 << K0) | (1 << K1));
+            if (!(thr_ok && (uint32_t(r) & cmr) == cmr)) continue;
+            const cx a = x[r];
+            x[r] = x[r2];
+            x[r2] = a;
+        }
+    }
+
+    // SWAP of lane bit b with register bit K
+    template <int K>
+    static __device__ __forceinline__ void swap_lr(cx (&x)[R], int b, uint32_t lane, bool thr_ok, uint32_t cmr) {
+        const int mask = 1 << b;
+        const bool lb = (lane >> b) & 1u;
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            if (r & (1 << K)) continue;
+            const int r1 = r | (1 << K);
+            // (lane bit, reg bit) of x[r] is (lb, 0), of x[r1] (lb, 1); the
+            // partner of (1,0) is (0,1) at lane ^ b, register r1, and back
+            const cx from_r1 = A::shfl(x[r1], mask);
+            const cx from_r = A::shfl(x[r], mask);
+            if (!(thr_ok && (uint32_t(r) & cmr) == cmr)) continue;
+            if (lb) x[r] = from_r1;
+            else x[r1] = from_r;
+        }
+    }
+
+    // SWAP of two lane bits
+    static __device__ __forceinline__ void swap_ll(cx (&x)[R], int b0, int b1, uint32_t lane, bool thr_ok,
+                                                   uint32_t cmr) {
+        const int mask = (1 << b0) | (1 << b1);
+        const bool differ = ((lane >> b0) ^ (lane >> b1)) & 1u;
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const cx p = A::shfl(x[r], mask);
+            if (differ && thr_ok && (uint32_t(r) & cmr) == cmr) x[r] = p;
+        }
+    }
+};
+
+template <class A, int RB>
+__global__ void __launch_bounds__(256) k_pass_reg(typename A::amp_t* __restrict__ dst,
+                                                   const typename A::amp_t* __restrict__ src, const DevPass dp,
+                                                   const DevOp* __restrict__ ops,
+                                                   const uint32_t* __restrict__ worklist) {
+    using amp_t = typename A::amp_t;
+    using cx = typename A::cx;
+    using RO = RegOps<A, RB>;
+    constexpr int R = 1 << RB;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    amp_t* tile = reinterpret_cast<amp_t*>(smem_raw);
+    __shared__ uint64_t choff[1 << kMaxTileHigh];
+
+    const uint32_t lane = threadIdx.x & 31u, wid = threadIdx.x >> 5;
+    const uint32_t gi = blockIdx.x >> dp.tpg_log2;
+    const uint32_t tau = blockIdx.x & ((1u << dp.tpg_log2) - 1u);
+    uint32_t g;
+    if (worklist != nullptr) {
+        g = worklist[gi];
+    } else {
+        g = gi;  // gi-th partition index with the coupling bits M cleared
+        uint32_t M = dp.M;
+        while (M) {
+            const uint32_t b = uint32_t(__ffs(M) - 1);
+            M &= M - 1;
+            const uint32_t lowm = (1u << b) - 1u;
+            g = ((g & ~lowm) << 1) | (g & lowm);
+        }
+    }
+    uint64_t xb = uint64_t(tau) << dp.lt;
+#pragma unroll
+    for (int k = 0; k < kMaxTileHigh; ++k) {
+        if (k < dp.nins) {
+            const uint32_t b = uint32_t(dp.ins[k]);
+            const uint64_t lowm = (uint64_t(1) << b) - 1u;
+            xb = ((xb & ~lowm) << 1) | (xb & lowm);
+        }
+    }
+    const uint64_t base = (uint64_t(g) << dp.p) | xb;
+    for (uint32_t c = threadIdx.x; c < (1u << dp.nh); c += blockDim.x) {
+        uint64_t off = 0;
+#pragma unroll
+        for (int k = 0; k < kMaxTileHigh; ++k)
+            if (k < dp.nh && ((c >> k) & 1u)) off |= uint64_t(1) << dp.h[k];
+        choff[c] = off;
+    }
+
+    // initial layout
+    int regpos[RB];
+#pragma unroll
+    for (int k = 0; k < RB; ++k) regpos[k] = dp.layout[k];
+    uint32_t jw = lane;
+#pragma unroll
+    for (int w = 0; w < 3; ++w)
+        if (w < dp.nwarp && ((wid >> w) & 1u)) jw |= 1u << dp.layout[RB + w];
+    auto joff = [&](int r) {
+        uint32_t o = 0;
+#pragma unroll
+        for (int k = 0; k < RB; ++k)
+            if ((r >> k) & 1) o |= 1u << regpos[k];
+        return o;
+    };
+    __syncthreads();
+
+    const uint32_t lowmask = (1u << dp.lt) - 1u;
+    cx x[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const uint32_t j = jw | joff(r);
+        x[r] = A::ld(src[base | choff[j >> dp.lt] | (j & lowmask)]);
+    }
+
+    const DevOp* pops = ops + dp.op_offset;
+    for (int oi = 0; oi < dp.nops; ++oi) {
+        const DevOp* op = pops + oi;
+        const int kind = op->kind;
+        if (kind == OP_PERM) {
+            __syncthreads();  // the previous layout change has been read by all
+#pragma unroll
+            for (int r = 0; r < R; ++r) tile[jw | joff(r)] = A::st(x[r]);
+            __syncthreads();
+#pragma unroll
+            for (int k = 0; k < RB; ++k) regpos[k] = op->perm[k];
+            jw = lane;
+#pragma unroll
+            for (int w = 0; w < 3; ++w)
+                if (w < op->nwarp && ((wid >> w) & 1u)) jw |= 1u << op->perm[RB + w];
+#pragma unroll
+            for (int r = 0; r < R; ++r) x[r] = A::ld(tile[jw | joff(r)]);
+            continue;
+        }
+        const uint64_t cmg = op->cm_glob;
+        if ((base & cmg) != cmg) continue;  // a control outside the tile is 0: uniform skip
+        const uint32_t cmt = op->cm_thr;
+        const uint32_t cmr = op->cm_reg;
+        const bool thr_ok = (jw & cmt) == cmt;
+        const int role0 = op->role0;
+        switch (kind) {
+            case OP_DENSE:
+            case OP_REAL:
+            case OP_X:
+            case OP_ANTI:
+                if (role0 >= kRoleLane) {
+                    RO::pair_lane(kind, x, op, role0 - kRoleLane, lane, thr_ok, cmr);
+                } else {
+                    dispatch_k<RB>(role0, [&](auto kc) {
+                        RO::template pair_reg<decltype(kc)::value>(kind, x, op, thr_ok, cmr);
+                    });
+                }
+                break;
+            case OP_SWAP: {
+                const int role1 = op->role1;
+                if (role0 >= kRoleLane && role1 >= kRoleLane) {
+                    RO::swap_ll(x, role0 - kRoleLane, role1 - kRoleLane, lane, thr_ok, cmr);
+                } else if (role0 >= kRoleLane || role1 >= kRoleLane) {
+                    const int b = (role0 >= kRoleLane ? role0 : role1) - kRoleLane;
+                    const int k = role0 >= kRoleLane ? role1 : role0;
+                    dispatch_k<RB>(k, [&](auto kc) {
+                        RO::template swap_lr<decltype(kc)::value>(x, b, lane, thr_ok, cmr);
+                    });
+                } else {
+                    const int k0 = role0 < role1 ? role0 : role1;
+                    const int k1 = role0 < role1 ? role1 : role0;
+                    dispatch_k<RB>(k0, [&](auto a) {
+                        dispatch_k<RB>(k1, [&](auto b) {
+                            constexpr int K0 = decltype(a)::value, K1 = decltype(b)::value;
+                            if constexpr (K0 < K1) RO::template swap_rr<K0, K1>(x, thr_ok, cmr);
+                        });
+                    });
+                }
+                break;
+            }
+            case OP_DIAG: {
+                const cx d0 = A::matp(op, 0), d1 = A::matp(op, 1);
+                if (role0 == kRoleNone) {
+                    const cx d = ((base >> op->gq) & 1) ? d1 : d0;
+#pragma unroll
+                    for (int r = 0; r < R; ++r)
+                        if (thr_ok && (uint32_t(r) & cmr) == cmr) x[r] = A::mul(d, x[r]);
+                } else if (role0 >= kRoleThread) {
+                    const cx d = ((jw >> (role0 - kRoleThread)) & 1u) ? d1 : d0;
+#pragma unroll
+                    for (int r = 0; r < R; ++r)
+                        if (thr_ok && (uint32_t(r) & cmr) == cmr) x[r] = A::mul(d, x[r]);
+                } else {
+#pragma unroll
+                    for (int r = 0; r < R; ++r)
+                        if (thr_ok && (uint32_t(r) & cmr) == cmr) x[r] = A::mul(((r >> role0) & 1) ? d1 : d0, x[r]);
+                }
+                break;
+            }
+            case OP_PHASE: {
+                const int sub = op->sub;
+                const cx f = A::matp(op, 0);
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    if (!(thr_ok && (uint32_t(r) & cmr) == cmr)) continue;
+                    if (sub == PH_NEG) x[r] = A::neg(x[r]);
+                    else if (sub == PH_POS_I) x[r] = A::mul_i(x[r]);
+                    else if (sub == PH_NEG_I) x[r] = A::mul_negi(x[r]);
+                    else x[r] = A::mul(f, x[r]);
+                }
+                break;
+            }
+            default:
+                break;
+        }
+    }
+
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const uint32_t j = jw | joff(r);
+        dst[base | choff[j >> dp.lt] | (j & lowmask)] = A::st(x[r]);
+    }
+}
+
+template <class A, int RB>
+int launch_reg_t(void* dst, const void* src, const DevPass& dp, const DevOp* ops, const uint32_t* worklist,
+                 uint32_t ngroups, cudaStream_t st) {
+    using amp_t = typename A::amp_t;
+    const size_t smem = sizeof(amp_t) << (dp.lt + dp.nh);
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaError_t e =
+            cudaFuncSetAttribute(k_pass_reg<A, RB>, cudaFuncAttributeMaxDynamicSharedMemorySize, 128 * 1024);
+        if (e != cudaSuccess) return int(e);
+        attr_set = true;
+    }
+    const uint64_t nblocks = uint64_t(ngroups) << dp.tpg_log2;
+    if (nblocks == 0) return 0;
+    const unsigned threads = 32u << dp.nwarp;
+    if (nblocks > 0x7fffffffull || smem > 128 * 1024 || dp.nreg != RB) return int(cudaErrorInvalidConfiguration);
+    k_pass_reg<A, RB><<<unsigned(nblocks), threads, smem, st>>>(static_cast<amp_t*>(dst),
+                                                                static_cast<const amp_t*>(src), dp, ops, worklist);
+    return int(cudaGetLastError());
+}
+
+template <class A>
+int launch_reg_a(void* dst, const void* src, const DevPass& dp, const DevOp* ops, const uint32_t* worklist,
+                 uint32_t ngroups, cudaStream_t st) {
+    switch (dp.nreg) {
+        case 2: return launch_reg_t<A, 2>(dst, src, dp, ops, worklist, ngroups, st);
+        case 3: return launch_reg_t<A, 3>(dst, src, dp, ops, worklist, ngroups, st);
+        case 4: return launch_reg_t<A, 4>(dst, src, dp, ops, worklist, ngroups, st);
+        case 5: return launch_reg_t<A, 5>(dst, src, dp, ops, worklist, ngroups, st);
+        default: return int(cudaErrorInvalidConfiguration);
+    }
+}
+
+int launch_pass_reg(int dtype, void* dst, const void* src, const DevPass& dp, const DevOp* ops,
+                    const uint32_t* worklist, uint32_t ngroups, void* stream) {
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    switch (dtype) {
+        case QT_C128: return launch_reg_a<ArF64>(dst, src, dp, ops, worklist, ngroups, st);
+        case QT_C64: return launch_reg_a<ArF32>(dst, src, dp, ops, worklist, ngroups, st);
+        case QT_C128_DF: return launch_reg_a<ArDF>(dst, src, dp, ops, worklist, ngroups, st);
+        default: return int(cudaErrorInvalidValue);
+    }
+}
+
+}  // namespace qt

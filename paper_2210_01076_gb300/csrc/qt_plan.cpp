@@ -270,6 +270,10 @@ SegPlan plan_segment(const std::vector<const qt_gate*>& gates, const PlanParams&
             }
             uint64_t nH = H | it.need;
             bool fits = popcount64(nH) <= pp.nh_max;
+            // The first unscheduled gate always starts a pass, even when its
+            // targets exceed nh_max (a SWAP on two high qubits with
+            // nh_max = 1): every sweep makes progress.
+            if (ops.empty() && ps.ngates == 0) fits = true;
             if (!pp.fusion && !ops.empty()) fits = false;
             if (!fits) {
                 blocked |= it.qubits;
@@ -411,6 +415,117 @@ void close_all(Bitset* W, const std::vector<Pass>& passes, const std::vector<Bit
             changed = mark_groups(W, T, passes[i].M) || changed;
         }
     }
+}
+
+// ------------------------------------------------ register-kernel layout --
+// The register kernel holds tile bits 0-4 in the lane id; of the other tile
+// bits, nreg are register-index bits and nwarp warp-id bits.  An op whose
+// target is a warp bit cannot run in place, so the ops are walked in order
+// and, before the first op whose targets are not all lane or register bits,
+// an OP_PERM moves to a layout whose register bits hold that op's targets and
+// as many of the following ops' targets as fit (then bits of the old layout,
+// then the highest tile bits).
+void plan_register_layout(DevPass* dp, std::vector<DevOp>* ops_io) {
+    const int tb = dp->lt + dp->nh;
+    dp->reg_kernel = 0;
+    if (tb < 7) return;
+    const int nreg = std::min(5, std::max(2, tb - 8));
+    const int nwarp = tb - 5 - nreg;
+    dp->reg_kernel = 1;
+    dp->nreg = nreg;
+    dp->nwarp = nwarp;
+    std::vector<DevOp>& ops = *ops_io;
+    const uint32_t upper = ((1u << tb) - 1u) & ~31u;
+    auto need = [&](const DevOp& o) -> uint32_t {
+        uint32_t m = 0;
+        switch (o.kind) {
+            case OP_DENSE: case OP_REAL: case OP_X: case OP_ANTI:
+                if (o.b0 >= 5) m |= 1u << o.b0;
+                break;
+            case OP_SWAP:
+                if (o.b0 >= 5) m |= 1u << o.b0;
+                if (o.b1 >= 5) m |= 1u << o.b1;
+                break;
+            default: break;
+        }
+        return m;
+    };
+    auto pc = [](uint32_t x) { return __builtin_popcount(x); };
+    auto choose = [&](size_t i, uint32_t keep) -> uint32_t {
+        uint32_t s = i < ops.size() ? need(ops[i]) : 0u;
+        for (size_t j = i + 1; j < ops.size() && pc(s) < nreg; ++j) {
+            const uint32_t t = s | need(ops[j]);
+            if (pc(t) > nreg) break;
+            s = t;
+        }
+        for (int b = tb - 1; b >= 5 && pc(s) < nreg; --b)
+            if ((keep >> b) & 1u) s |= 1u << b;
+        for (int b = tb - 1; b >= 5 && pc(s) < nreg; --b)
+            if ((upper >> b) & 1u) s |= 1u << b;
+        return s;
+    };
+    auto fill = [&](uint32_t regset, int32_t* out32, int8_t* out8) {
+        int k = 0;
+        for (int b = 5; b < tb; ++b)
+            if ((regset >> b) & 1u) {
+                if (out32) out32[k] = b;
+                if (out8) out8[k] = int8_t(b);
+                ++k;
+            }
+        for (int b = 5; b < tb; ++b)
+            if (((upper & ~regset) >> b) & 1u) {
+                if (out32) out32[k] = b;
+                if (out8) out8[k] = int8_t(b);
+                ++k;
+            }
+    };
+    uint32_t cur = choose(0, 0);
+    fill(cur, dp->layout, nullptr);
+    std::vector<DevOp> out;
+    out.reserve(ops.size() + 4);
+    for (size_t i = 0; i < ops.size(); ++i) {
+        DevOp o = ops[i];
+        if (need(o) & ~cur) {
+            cur = choose(i, cur);
+            DevOp pm;
+            std::memset(&pm, 0, sizeof pm);
+            pm.kind = OP_PERM;
+            pm.nreg = int8_t(nreg);
+            pm.nwarp = int8_t(nwarp);
+            fill(cur, nullptr, pm.perm);
+            out.push_back(pm);
+        }
+        auto regidx = [&](int b) { return int8_t(pc(cur & ((1u << b) - 1u))); };
+        auto target_role = [&](int b) -> int8_t {
+            if (b < 0) return kRoleNone;
+            if (b < 5) return int8_t(kRoleLane + b);
+            return regidx(b);  // need() put it in the register bits
+        };
+        if (o.kind == OP_DIAG) {
+            if (o.b0 < 0) o.role0 = kRoleNone;
+            else if ((cur >> o.b0) & 1u) o.role0 = regidx(o.b0);
+            else o.role0 = int8_t(kRoleThread + o.b0);
+            o.role1 = kRoleNone;
+        } else if (o.kind == OP_PHASE) {
+            o.role0 = o.role1 = kRoleNone;
+        } else {
+            o.role0 = target_role(o.b0);
+            o.role1 = o.kind == OP_SWAP ? target_role(o.b1) : kRoleNone;
+        }
+        // split the tile-local control mask (held in cm_thr on entry)
+        const uint32_t cmt = o.cm_thr;
+        uint32_t thr = 0;
+        uint16_t reg = 0;
+        for (int b = 0; b < tb; ++b) {
+            if (!((cmt >> b) & 1u)) continue;
+            if ((cur >> b) & 1u) reg |= uint16_t(1u << regidx(b));
+            else thr |= 1u << b;
+        }
+        o.cm_thr = thr;
+        o.cm_reg = reg;
+        out.push_back(o);
+    }
+    ops.swap(out);
 }
 
 }  // namespace qt

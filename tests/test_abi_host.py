@@ -220,3 +220,18 @@ def test_no_gpu_update_fails_loudly():
     with pytest.raises(B.QtError) as e:
         c.update_state()
     assert e.value.status == B.QT_ERR_CUDA
+
+
+@pytest.mark.timeout(60)
+@pytest.mark.parametrize("tile_high", [0, 1, 2])
+def test_planner_makes_progress_when_a_gate_exceeds_the_tile(tile_high):
+    """A SWAP on two qubits above the tile's low run needs two tile qubits;
+    with tile_high < 2 it still gets a pass of its own."""
+    n, p = 12, 8
+    c = dry(n, p, G=2)
+    c.set_option("tile_high", tile_high)
+    levels = [[W.make_gate("swap", [9, 11]), W.make_gate("h", [0])], [W.make_gate("ccx", [10, 7, 8])],
+              [W.make_gate("swap", [6, 10])]]
+    c.load_levels(levels)
+    st = c.update_state()
+    assert st["passes_total"] >= 3 and st["amp_updates"] == 4 * (1 << n)

@@ -49,12 +49,39 @@ def test_each_gate_every_position(dtype, name):
 
 
 @pytest.mark.parametrize("dtype", DTYPES)
-@pytest.mark.parametrize("fusion,tile_high", [(0, 6), (1, 1), (1, 3), (1, 6)])
-def test_random_circuit_config1_shape(dtype, fusion, tile_high):
+@pytest.mark.parametrize("name", ALL)
+def test_each_gate_register_kernel_roles(dtype, name):
+    """Every gate kind on ordered tuples of qubits that land on every role of
+    the register kernel: lane bits (q < 5), register and warp bits (tile
+    qubits >= 5, layouts changed by OP_PERM), and qubits outside the tile
+    (controls and diagonals uniform over a tile), with partitions of 2^7 so
+    that tiles also couple partitions."""
+    n, p = 10, 7
+    qubits = [0, 3, 5, 6, 8, 9]
+    nq = sum(W.ARITY[name][:2])
+    rng = np.random.default_rng(abs(hash((name, dtype, "reg"))) % 2**32)
+    prep = prep_levels(n, seed=4)
+    for qs in itertools.permutations(qubits, nq):
+        g = W.make_gate(name, qs, rng.uniform(0, 2 * math.pi, W.ARITY[name][2]))
+        # a few neighbours in the same pass so that layouts change around it
+        extra = [W.make_gate("h", [q]) for q in range(n) if q not in qs][:3]
+        levels = prep + [[g] + extra, [W.make_gate("rx", [qs[0]], [0.4])]]
+        want = oracle.simulate(n, W.flatten(levels))
+        for tile_high in (2, 4):
+            c, _ = build_circuit(n, levels, dtype, p, tile_high=tile_high)
+            c.update_state()
+            assert max_err(c.read_amplitudes(), want) <= TOL[dtype], (name, qs, tile_high)
+            c.close()
+
+
+@pytest.mark.parametrize("dtype", DTYPES)
+@pytest.mark.parametrize("fusion,tile_high,reg", [(0, 6, 1), (1, 1, 1), (1, 3, 1), (1, 6, 1), (1, 6, 0),
+                                                   (1, 2, 0)])
+def test_random_circuit_config1_shape(dtype, fusion, tile_high, reg):
     """n = 12, 200 gates uniform over the 14 kinds, partitions of 2^8."""
     n, p = 12, 8
     levels = W.random_circuit(n, 200, seed=11)
-    c, _ = build_circuit(n, levels, dtype, p, fusion=fusion, tile_high=tile_high)
+    c, _ = build_circuit(n, levels, dtype, p, fusion=fusion, tile_high=tile_high, reg_kernel=reg)
     st = c.update_state()
     assert st["amp_updates"] == 200 * (1 << n)
     got = c.read_amplitudes()
