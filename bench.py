@@ -144,6 +144,12 @@ def make_workload(seed, rounds):
     return levels, model, stream_model, edits
 
 
+def config_dict(world):
+    return {"workload": WORKLOAD, "n_qubits": N_QUBITS, "gates": N_GATES, "log2_partition": LOG2_PART,
+            "ckpt_interval_levels": CKPT, "edits_per_round": "1-5", "parallelism": f"replicas{world}",
+            "l2": "inputs larger than L2: state 256 MiB, checkpoints ~9.5 GiB; no flush"}
+
+
 def pctl(xs, q):
     return float(np.percentile(np.asarray(xs), q)) if xs else None
 
@@ -304,9 +310,7 @@ def run_ours(args):
             "vs_baseline": None,
             "dtype": "c128 (float-float arithmetic)",
             "data": "synthetic (seeded random circuits and edit streams)",
-            "config": {"workload": WORKLOAD, "n_qubits": N_QUBITS, "gates": N_GATES, "log2_partition": LOG2_PART,
-                       "ckpt_interval_levels": CKPT, "edits_per_round": "1-5", "parallelism": f"replicas{world}",
-                       "l2": "state 256 MiB > L2, checkpoints 1.8 GB: no flush"},
+            "config": config_dict(world),
             "hbm_gbs": hbm / (t_max * 1e-3) / 1e9,
             "incremental_latency_ms": {"p50": pctl(inc_lat, 50), "p99": pctl(inc_lat, 99)},
             "full_resim_latency_ms": {"p50": pctl(fulls, 50), "p99": pctl(fulls, 99)},
@@ -386,7 +390,7 @@ def run_reference(args):
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3 / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic (seeded random circuits)",
-        "config": {"workload": WORKLOAD, "n_qubits": N_QUBITS, "gates": N_GATES, "log2_partition": LOG2_PART},
+        "config": config_dict(world),
         "cpu_baseline": {"value": value, "unit": "amp-updates/s", "cores": nth, "kind": "oracle",
                          "sample": f"{per_step} gates of the n=24 circuit per step (a CPU re-simulation "
                                    f"re-runs every gate after the edit)"},
@@ -396,6 +400,7 @@ def run_reference(args):
 
 
 def main():
+    global N_QUBITS, CKPT
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=30)
@@ -409,7 +414,6 @@ def main():
     ap.add_argument("--ckpt", type=int, default=CKPT, help="levels per checkpoint segment")
     ap.add_argument("--option", action="append", default=[], help="extra qt_set_option key=value")
     args = ap.parse_args()
-    global N_QUBITS, CKPT
     N_QUBITS, CKPT = args.n_qubits, args.ckpt
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3
