@@ -25,6 +25,7 @@
 #include <chrono>
 #include <cstring>
 #include <new>
+#include <stdexcept>
 #include <string>
 #include <vector>
 
@@ -60,7 +61,7 @@ struct qt_circuit {
     // options
     int ckpt_interval = 4;
     bool fusion = true;
-    int tile_high = 6;
+    int tile_high = 5;  // tiles of 2^11 (complex128) / 2^12 (complex64) amplitudes
     int64_t mem_limit = 0;
     bool kernel_timing = false;
     bool dry_run = false;
@@ -262,6 +263,10 @@ DevOp encode_op(int dtype, const Pass& ps, const HostOp& op) {
     uint64_t tile_mask = (uint64_t(1) << ps.lt) - 1;
     for (int k = 0; k < ps.nh; ++k) tile_mask |= uint64_t(1) << ps.h[k];
     d.kind = op.kind;
+    // Only X, SWAP and PHASE ops carry conditions (CNOT/CCX, CZ/CP lower to
+    // them); the register kernel applies the other kinds unpredicated.
+    if (op.cmask != 0 && op.kind != OP_X && op.kind != OP_SWAP && op.kind != OP_PHASE)
+        throw std::logic_error("controlled op of a kind that takes no controls");
     d.cm_glob = op.cmask & ~tile_mask;
     std::vector<std::pair<int, int>> fixed;  // (tile-local position, value)
     for (int q = 0; q < 64; ++q)

@@ -9,14 +9,16 @@
 //                  (register index r) | warp bits (warp id)
 //
 // so a warp always holds 32 consecutive amplitudes (coalesced loads and
-// stores, conflict-free shared memory).  An op whose target is a register bit
-// pairs registers of the same thread; a target that is a lane bit exchanges
-// the partner amplitude with a warp shuffle (the low-stride qubits); the host
-// inserts an OP_PERM before an op whose target is a warp bit, which rewrites
-// the layout through shared memory (one read and one write of the tile) so
-// that the target becomes a register bit.  Diagonal ops, phases and controls
-// need no particular layout: each thread knows the index of every amplitude
-// it holds.
+// stores, conflict-free shared memory).  An op whose target is a lane bit
+// exchanges the partner amplitude with a warp shuffle (the low-stride
+// qubits).  An op whose target is register bit k first exchanges register
+// bits 0 and k (register moves, resolved at compile time) so that one copy of
+// each op's code serves every register bit, which keeps the kernel small
+// enough for the instruction cache.  Before an op whose target is a warp bit
+// the host inserts an OP_PERM, which rewrites the layout through shared
+// memory (one read and one write of the tile).  Diagonal ops, phases and
+// controls need no particular layout: each thread knows the index of every
+// amplitude it holds.
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -51,70 +53,90 @@ __device__ __forceinline__ void dispatch_k(int k, F&& f) {
     }
 }
 
+// Register layout: tile bit of register-index bit k, packed 5 bits per k.
+__device__ __forceinline__ uint32_t field5(uint32_t packed, int k) { return (packed >> (5 * k)) & 31u; }
+
 template <class A, int RB>
 struct RegOps {
     using cx = typename A::cx;
     static constexpr int R = 1 << RB;
 
-    // one-target ops on register bit K: (x[r], x[r | 2^K]) for r with bit K = 0
+    // exchange register-index bits 0 and K (K > 0)
     template <int K>
-    static __device__ __forceinline__ void pair_reg(int kind, cx (&x)[R], const DevOp* op, bool thr_ok,
-                                                    uint32_t cmr) {
-        if (kind == OP_DENSE || kind == OP_REAL) {
-            const cx u00 = A::matp(op, 0), u01 = A::matp(op, 1), u10 = A::matp(op, 2), u11 = A::matp(op, 3);
+    static __device__ __forceinline__ void swap_bits(cx (&x)[R]) {
 #pragma unroll
-            for (int r = 0; r < R; ++r) {
-                if (r & (1 << K)) continue;
-                const int r1 = r | (1 << K);
-                if (!(thr_ok && (uint32_t(r) & cmr) == cmr)) continue;
-                const cx a = x[r], b = x[r1];
-                if (kind == OP_DENSE) {
-                    x[r] = A::lin2(u00, a, u01, b);
-                    x[r1] = A::lin2(u10, a, u11, b);
-                } else {
-                    x[r] = A::lin2r(u00, a, u01, b);
-                    x[r1] = A::lin2r(u10, a, u11, b);
-                }
-            }
-        } else if (kind == OP_X) {
-#pragma unroll
-            for (int r = 0; r < R; ++r) {
-                if (r & (1 << K)) continue;
-                const int r1 = r | (1 << K);
-                if (!(thr_ok && (uint32_t(r) & cmr) == cmr)) continue;
-                const cx a = x[r];
-                x[r] = x[r1];
-                x[r1] = a;
-            }
-        } else {  // OP_ANTI
-            const cx m01 = A::matp(op, 0), m10 = A::matp(op, 1);
-#pragma unroll
-            for (int r = 0; r < R; ++r) {
-                if (r & (1 << K)) continue;
-                const int r1 = r | (1 << K);
-                if (!(thr_ok && (uint32_t(r) & cmr) == cmr)) continue;
-                const cx a = x[r], b = x[r1];
-                x[r] = A::mul(m01, b);
-                x[r1] = A::mul(m10, a);
+        for (int r = 0; r < R; ++r) {
+            if ((r & 1) && !((r >> K) & 1)) {
+                const int r2 = r ^ (1 | (1 << K));
+                const cx t = x[r];
+                x[r] = x[r2];
+                x[r2] = t;
             }
         }
     }
 
-    // one-target ops on lane bit b: the partner amplitude comes from lane ^ 2^b
+    // one-target ops on register bit 0: pairs (x[2i], x[2i+1]).  DENSE, REAL,
+    // ANTI and DIAG ops never carry controls (only X, SWAP and PHASE do; the
+    // host checks it), so their loops need no per-amplitude predicate.
+    static __device__ __forceinline__ void pair_reg0(int kind, cx (&x)[R], const DevOp* op, bool thr_ok,
+                                                     uint32_t cmr) {
+        if (kind == OP_DENSE) {
+            const cx u00 = A::matp(op, 0), u01 = A::matp(op, 1), u10 = A::matp(op, 2), u11 = A::matp(op, 3);
+#pragma unroll
+            for (int r = 0; r < R; r += 2) {
+                const cx a = x[r], b = x[r + 1];
+                x[r] = A::lin2(u00, a, u01, b);
+                x[r + 1] = A::lin2(u10, a, u11, b);
+            }
+        } else if (kind == OP_REAL) {
+            const cx u00 = A::matp(op, 0), u01 = A::matp(op, 1), u10 = A::matp(op, 2), u11 = A::matp(op, 3);
+#pragma unroll
+            for (int r = 0; r < R; r += 2) {
+                const cx a = x[r], b = x[r + 1];
+                x[r] = A::lin2r(u00, a, u01, b);
+                x[r + 1] = A::lin2r(u10, a, u11, b);
+            }
+        } else if (kind == OP_X) {
+#pragma unroll
+            for (int r = 0; r < R; r += 2) {
+                if (!(thr_ok && (uint32_t(r) & cmr) == cmr)) continue;
+                const cx a = x[r];
+                x[r] = x[r + 1];
+                x[r + 1] = a;
+            }
+        } else {  // OP_ANTI
+            const cx m01 = A::matp(op, 0), m10 = A::matp(op, 1);
+#pragma unroll
+            for (int r = 0; r < R; r += 2) {
+                const cx a = x[r], b = x[r + 1];
+                x[r] = A::mul(m01, b);
+                x[r + 1] = A::mul(m10, a);
+            }
+        }
+    }
+
+    // one-target ops on lane bit b: the partner amplitude p comes from lane ^
+    // 2^b.  A lane whose bit is 0 computes u00 x + u01 p, a lane whose bit is
+    // 1 computes u11 x + u10 p: the coefficients are chosen once per op.
     static __device__ __forceinline__ void pair_lane(int kind, cx (&x)[R], const DevOp* op, int b, uint32_t lane,
                                                      bool thr_ok, uint32_t cmr) {
         const int mask = 1 << b;
         const bool hi = (lane >> b) & 1u;
         if (kind == OP_DENSE || kind == OP_REAL) {
-            // the bit-0 output is u00 a0 + u01 a1, the bit-1 output u10 a0 + u11 a1
-            const cx c0 = A::sel(hi, A::matp(op, 2), A::matp(op, 0));
-            const cx c1 = A::sel(hi, A::matp(op, 3), A::matp(op, 1));
+            const cx cs = A::sel(hi, A::matp(op, 3), A::matp(op, 0));  // coefficient of the own amplitude
+            const cx cp = A::sel(hi, A::matp(op, 2), A::matp(op, 1));  // coefficient of the partner's
+            if (kind == OP_DENSE) {
 #pragma unroll
-            for (int r = 0; r < R; ++r) {
-                const cx p = A::shfl(x[r], mask);
-                const cx a0 = A::sel(hi, p, x[r]), a1 = A::sel(hi, x[r], p);
-                const cx y = (kind == OP_DENSE) ? A::lin2(c0, a0, c1, a1) : A::lin2r(c0, a0, c1, a1);
-                if (thr_ok && (uint32_t(r) & cmr) == cmr) x[r] = y;
+                for (int r = 0; r < R; ++r) {
+                    const cx p = A::shfl(x[r], mask);
+                    x[r] = A::lin2(cs, x[r], cp, p);
+                }
+            } else {
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    const cx p = A::shfl(x[r], mask);
+                    x[r] = A::lin2r(cs, x[r], cp, p);
+                }
             }
         } else if (kind == OP_X) {
 #pragma unroll
@@ -127,8 +149,7 @@ struct RegOps {
 #pragma unroll
             for (int r = 0; r < R; ++r) {
                 const cx p = A::shfl(x[r], mask);
-                const cx y = A::mul(c, p);
-                if (thr_ok && (uint32_t(r) & cmr) == cmr) x[r] = y;
+                x[r] = A::mul(c, p);
             }
         }
     }
@@ -175,6 +196,44 @@ struct RegOps {
         for (int r = 0; r < R; ++r) {
             const cx p = A::shfl(x[r], mask);
             if (differ && thr_ok && (uint32_t(r) & cmr) == cmr) x[r] = p;
+        }
+    }
+
+    // diag(d0, d1) on a qubit whose value for x[r] is bit k of r (k >= 0) or
+    // the per-thread bit tb (k < 0)
+    static __device__ __forceinline__ void diag(cx (&x)[R], const DevOp* op, int k, bool tbit) {
+        const cx d0 = A::matp(op, 0), d1 = A::matp(op, 1);
+        if (k < 0) {
+            const cx d = A::sel(tbit, d1, d0);
+#pragma unroll
+            for (int r = 0; r < R; ++r) x[r] = A::mul(d, x[r]);
+        } else {
+#pragma unroll
+            for (int r = 0; r < R; ++r) x[r] = A::mul(A::sel((r >> k) & 1, d1, d0), x[r]);
+        }
+    }
+
+    static __device__ __forceinline__ void phase(cx (&x)[R], const DevOp* op, bool thr_ok, uint32_t cmr) {
+        const int sub = op->sub;
+        if (sub == PH_NEG) {
+#pragma unroll
+            for (int r = 0; r < R; ++r)
+                if (thr_ok && (uint32_t(r) & cmr) == cmr) x[r] = A::neg(x[r]);
+        } else if (sub == PH_POS_I) {
+#pragma unroll
+            for (int r = 0; r < R; ++r)
+                if (thr_ok && (uint32_t(r) & cmr) == cmr) x[r] = A::mul_i(x[r]);
+        } else if (sub == PH_NEG_I) {
+#pragma unroll
+            for (int r = 0; r < R; ++r)
+                if (thr_ok && (uint32_t(r) & cmr) == cmr) x[r] = A::mul_negi(x[r]);
+        } else {
+            const cx f = A::matp(op, 0);
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                if (!(thr_ok && (uint32_t(r) & cmr) == cmr)) continue;
+                x[r] = A::mul(f, x[r]);
+            }
         }
     }
 };
@@ -226,10 +285,10 @@ __global__ void __launch_bounds__(256) k_pass_reg(typename A::amp_t* __restrict_
         choff[c] = off;
     }
 
-    // initial layout
-    int regpos[RB];
+    // layout: register bit k <-> tile bit field5(rpos, k); warp bits in jw
+    uint32_t rpos = 0;
 #pragma unroll
-    for (int k = 0; k < RB; ++k) regpos[k] = dp.layout[k];
+    for (int k = 0; k < RB; ++k) rpos |= uint32_t(dp.layout[k]) << (5 * k);
     uint32_t jw = lane;
 #pragma unroll
     for (int w = 0; w < 3; ++w)
@@ -238,7 +297,7 @@ __global__ void __launch_bounds__(256) k_pass_reg(typename A::amp_t* __restrict_
         uint32_t o = 0;
 #pragma unroll
         for (int k = 0; k < RB; ++k)
-            if ((r >> k) & 1) o |= 1u << regpos[k];
+            if ((r >> k) & 1) o |= 1u << field5(rpos, k);
         return o;
     };
     __syncthreads();
@@ -260,8 +319,9 @@ __global__ void __launch_bounds__(256) k_pass_reg(typename A::amp_t* __restrict_
 #pragma unroll
             for (int r = 0; r < R; ++r) tile[jw | joff(r)] = A::st(x[r]);
             __syncthreads();
+            rpos = 0;
 #pragma unroll
-            for (int k = 0; k < RB; ++k) regpos[k] = op->perm[k];
+            for (int k = 0; k < RB; ++k) rpos |= uint32_t(op->perm[k]) << (5 * k);
             jw = lane;
 #pragma unroll
             for (int w = 0; w < 3; ++w)
@@ -270,24 +330,29 @@ __global__ void __launch_bounds__(256) k_pass_reg(typename A::amp_t* __restrict_
             for (int r = 0; r < R; ++r) x[r] = A::ld(tile[jw | joff(r)]);
             continue;
         }
+        const int role0 = op->role0;
+        if (kind <= OP_ANTI && kind != OP_DIAG && kind != OP_PHASE && role0 > 0 && role0 < kRoleLane) {
+            // target on register bit role0: bring it to register bit 0 (the
+            // host tracks the same exchange; it happens even when the op is
+            // skipped below, so the layout stays in step)
+            dispatch_k<RB>(role0, [&](auto kc) {
+                if constexpr (decltype(kc)::value > 0) RO::template swap_bits<decltype(kc)::value>(x);
+            });
+            const uint32_t a = field5(rpos, 0), b = field5(rpos, role0);
+            rpos = (rpos & ~(31u | (31u << (5 * role0)))) | b | (a << (5 * role0));
+        }
         const uint64_t cmg = op->cm_glob;
         if ((base & cmg) != cmg) continue;  // a control outside the tile is 0: uniform skip
         const uint32_t cmt = op->cm_thr;
         const uint32_t cmr = op->cm_reg;
         const bool thr_ok = (jw & cmt) == cmt;
-        const int role0 = op->role0;
         switch (kind) {
             case OP_DENSE:
             case OP_REAL:
             case OP_X:
             case OP_ANTI:
-                if (role0 >= kRoleLane) {
-                    RO::pair_lane(kind, x, op, role0 - kRoleLane, lane, thr_ok, cmr);
-                } else {
-                    dispatch_k<RB>(role0, [&](auto kc) {
-                        RO::template pair_reg<decltype(kc)::value>(kind, x, op, thr_ok, cmr);
-                    });
-                }
+                if (role0 >= kRoleLane) RO::pair_lane(kind, x, op, role0 - kRoleLane, lane, thr_ok, cmr);
+                else RO::pair_reg0(kind, x, op, thr_ok, cmr);
                 break;
             case OP_SWAP: {
                 const int role1 = op->role1;
@@ -312,37 +377,18 @@ __global__ void __launch_bounds__(256) k_pass_reg(typename A::amp_t* __restrict_
                 break;
             }
             case OP_DIAG: {
-                const cx d0 = A::matp(op, 0), d1 = A::matp(op, 1);
                 if (role0 == kRoleNone) {
-                    const cx d = ((base >> op->gq) & 1) ? d1 : d0;
-#pragma unroll
-                    for (int r = 0; r < R; ++r)
-                        if (thr_ok && (uint32_t(r) & cmr) == cmr) x[r] = A::mul(d, x[r]);
+                    RO::diag(x, op, -1, (base >> op->gq) & 1);
                 } else if (role0 >= kRoleThread) {
-                    const cx d = ((jw >> (role0 - kRoleThread)) & 1u) ? d1 : d0;
-#pragma unroll
-                    for (int r = 0; r < R; ++r)
-                        if (thr_ok && (uint32_t(r) & cmr) == cmr) x[r] = A::mul(d, x[r]);
+                    RO::diag(x, op, -1, (jw >> (role0 - kRoleThread)) & 1u);
                 } else {
-#pragma unroll
-                    for (int r = 0; r < R; ++r)
-                        if (thr_ok && (uint32_t(r) & cmr) == cmr) x[r] = A::mul(((r >> role0) & 1) ? d1 : d0, x[r]);
+                    RO::diag(x, op, role0, false);
                 }
                 break;
             }
-            case OP_PHASE: {
-                const int sub = op->sub;
-                const cx f = A::matp(op, 0);
-#pragma unroll
-                for (int r = 0; r < R; ++r) {
-                    if (!(thr_ok && (uint32_t(r) & cmr) == cmr)) continue;
-                    if (sub == PH_NEG) x[r] = A::neg(x[r]);
-                    else if (sub == PH_POS_I) x[r] = A::mul_i(x[r]);
-                    else if (sub == PH_NEG_I) x[r] = A::mul_negi(x[r]);
-                    else x[r] = A::mul(f, x[r]);
-                }
+            case OP_PHASE:
+                RO::phase(x, op, thr_ok, cmr);
                 break;
-            }
             default:
                 break;
         }

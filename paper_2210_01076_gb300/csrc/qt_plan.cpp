@@ -150,6 +150,23 @@ uint64_t op_qubits(const HostOp& op) {
 
 int popcount64(uint64_t x) { return __builtin_popcountll(x); }
 
+// Arithmetic per amplitude of an op in float-float (the costliest arithmetic;
+// the binary32 and binary64 kernels have the same proportions): a complex 2x2
+// is two 4-term dot products per amplitude, a real 2x2, a diagonal or an
+// anti-diagonal two 2-term ones, a general phase touches half the
+// amplitudes, exact phases (-1, +-i) and permutations only move data.
+int op_cost(const HostOp& op) {
+    switch (op.kind) {
+        case OP_DENSE: return 86;
+        case OP_REAL: case OP_DIAG: case OP_ANTI: return 38;
+        case OP_PHASE: {
+            const bool exact = (op.m[0] == -1.0 && op.m[1] == 0.0) || (op.m[0] == 0.0 && std::fabs(op.m[1]) == 1.0);
+            return exact ? 1 : 19;
+        }
+        default: return 1;
+    }
+}
+
 }  // namespace
 
 uint64_t gate_qubit_mask(const qt_gate& g) {
@@ -208,6 +225,25 @@ bool lower_gate(const qt_gate& g, int n, std::vector<HostOp>* out, std::string* 
     }
     uint64_t cmask = 0;
     for (int k = 0; k < g.ncontrol; ++k) cmask |= uint64_t(1) << g.control[k];
+    if ((g.kind == QT_RX || g.kind == QT_U3) && cmask == 0) {
+        // A complex 2x2 costs about twice a real one; write these as a real
+        // rotation between two phases (exact for RX):
+        //   U3(t,p,l) = diag(1, e^{ip}) RY(t) diag(1, e^{il})
+        //   RX(t)     = diag(1, -i)     RY(t) diag(1, i)
+        const double t = g.theta[0];
+        const double c = std::cos(t / 2.0), s = std::sin(t / 2.0);
+        const cd I(0.0, 1.0);
+        const cd first = g.kind == QT_RX ? I : std::polar(1.0, g.theta[2]);
+        const cd last = g.kind == QT_RX ? -I : std::polar(1.0, g.theta[1]);
+        M2 P1, RY, P2;
+        P1.a[0] = 1.0; P1.a[1] = 0.0; P1.a[2] = 0.0; P1.a[3] = first;
+        RY.a[0] = c; RY.a[1] = -s; RY.a[2] = s; RY.a[3] = c;
+        P2.a[0] = 1.0; P2.a[1] = 0.0; P2.a[2] = 0.0; P2.a[3] = last;
+        out->push_back(classify(P1, g.target[0], 0, 0));
+        out->push_back(classify(RY, g.target[0], 0, 1));
+        out->push_back(classify(P2, g.target[0], 0, 0));
+        return true;
+    }
     out->push_back(classify(U, g.target[0], cmask, 1));
     return true;
 }
@@ -296,8 +332,11 @@ SegPlan plan_segment(const std::vector<const qt_gate*>& gates, const PlanParams&
                 M2 a, b;
                 op_matrix(prev, &a);
                 op_matrix(op, &b);
-                prev = classify(mul(b, a), op.q0, 0, prev.ngates + op.ngates);
-                continue;
+                HostOp m = classify(mul(b, a), op.q0, 0, prev.ngates + op.ngates);
+                if (op_cost(m) <= op_cost(prev) + op_cost(op)) {  // merge only when it saves work
+                    prev = m;
+                    continue;
+                }
             }
             merged.push_back(op);
             for (int q = 0; q < pp.n; ++q)
@@ -479,10 +518,20 @@ void plan_register_layout(DevPass* dp, std::vector<DevOp>* ops_io) {
                 ++k;
             }
     };
+    // regs[k] = tile bit of register-index bit k (the kernel's order); a
+    // layout change sets them ascending, a pair op on register bit k > 0
+    // exchanges regs[0] and regs[k] (the kernel moves the registers to match)
     uint32_t cur = choose(0, 0);
     fill(cur, dp->layout, nullptr);
+    int regs[8];
+    for (int k = 0; k < nreg; ++k) regs[k] = dp->layout[k];
     std::vector<DevOp> out;
     out.reserve(ops.size() + 4);
+    auto regidx = [&](int b) -> int {
+        for (int k = 0; k < nreg; ++k)
+            if (regs[k] == b) return k;
+        return -1;
+    };
     for (size_t i = 0; i < ops.size(); ++i) {
         DevOp o = ops[i];
         if (need(o) & ~cur) {
@@ -493,32 +542,39 @@ void plan_register_layout(DevPass* dp, std::vector<DevOp>* ops_io) {
             pm.nreg = int8_t(nreg);
             pm.nwarp = int8_t(nwarp);
             fill(cur, nullptr, pm.perm);
+            for (int k = 0; k < nreg; ++k) regs[k] = pm.perm[k];
             out.push_back(pm);
         }
-        auto regidx = [&](int b) { return int8_t(pc(cur & ((1u << b) - 1u))); };
-        auto target_role = [&](int b) -> int8_t {
-            if (b < 0) return kRoleNone;
-            if (b < 5) return int8_t(kRoleLane + b);
-            return regidx(b);  // need() put it in the register bits
-        };
-        if (o.kind == OP_DIAG) {
+        const bool pair = o.kind == OP_DENSE || o.kind == OP_REAL || o.kind == OP_X || o.kind == OP_ANTI;
+        if (pair) {
+            if (o.b0 < 5) {
+                o.role0 = int8_t(kRoleLane + o.b0);
+            } else {
+                const int k = regidx(o.b0);
+                o.role0 = int8_t(k);
+                if (k > 0) std::swap(regs[0], regs[k]);
+            }
+            o.role1 = kRoleNone;
+        } else if (o.kind == OP_SWAP) {
+            o.role0 = o.b0 < 5 ? int8_t(kRoleLane + o.b0) : int8_t(regidx(o.b0));
+            o.role1 = o.b1 < 5 ? int8_t(kRoleLane + o.b1) : int8_t(regidx(o.b1));
+        } else if (o.kind == OP_DIAG) {
             if (o.b0 < 0) o.role0 = kRoleNone;
-            else if ((cur >> o.b0) & 1u) o.role0 = regidx(o.b0);
+            else if (o.b0 >= 5 && regidx(o.b0) >= 0) o.role0 = int8_t(regidx(o.b0));
             else o.role0 = int8_t(kRoleThread + o.b0);
             o.role1 = kRoleNone;
-        } else if (o.kind == OP_PHASE) {
-            o.role0 = o.role1 = kRoleNone;
         } else {
-            o.role0 = target_role(o.b0);
-            o.role1 = o.kind == OP_SWAP ? target_role(o.b1) : kRoleNone;
+            o.role0 = o.role1 = kRoleNone;
         }
-        // split the tile-local control mask (held in cm_thr on entry)
+        // split the tile-local control mask (held in cm_thr on entry) for the
+        // layout the op runs in
         const uint32_t cmt = o.cm_thr;
         uint32_t thr = 0;
         uint16_t reg = 0;
         for (int b = 0; b < tb; ++b) {
             if (!((cmt >> b) & 1u)) continue;
-            if ((cur >> b) & 1u) reg |= uint16_t(1u << regidx(b));
+            const int k = b >= 5 ? regidx(b) : -1;
+            if (k >= 0) reg |= uint16_t(1u << k);
             else thr |= 1u << b;
         }
         o.cm_thr = thr;
