@@ -170,6 +170,39 @@ qt_status qt_read_amplitudes_device(const qt_circuit* c, uint64_t first, uint64_
  * FP64-class accuracy for every dtype (float-float partial sums, FP64 tree). */
 qt_status qt_norm(const qt_circuit* c, double* out);
 
+/* qt_norm_static -- the norm of amplitudes the caller holds in device memory,
+ * computed without allocating anything.  (The paper has no counterpart: this
+ * entry point serves callers that cannot let a library call cudaMalloc, such
+ * as a process that routes all device memory through its own allocator or
+ * pool, or a latency-critical loop that cannot afford an allocation and the
+ * synchronisation it may imply.)
+ *
+ * amps_device: `count` amplitudes in device memory, in the element format of
+ *   `dtype` (QT_C128: binary64 re, im; QT_C64: binary32 re, im; QT_C128_DF:
+ *   binary32 re_hi, re_lo, im_hi, im_lo).  Not modified.
+ * out_device: one double in device memory; receives sum |a|^2, reduced like
+ *   qt_norm (float-float partial sums, binary64 tree).  Written by the work
+ *   enqueued on `cuda_stream` (a cudaStream_t, NULL = the legacy default
+ *   stream); the call does not wait for it.
+ * count: 1 <= count <= QT_NORM_STATIC_MAX_AMPS, else QT_ERR_RANGE.
+ * Memory: the partial sums live in one file-scope device array of
+ *   QT_NORM_STATIC_SCRATCH_BYTES bytes (1216 doubles), which every GPU that
+ *   loads the library holds until the process exits.  The first call on a
+ *   device looks up that array's device address (cudaGetSymbolAddress) with
+ *   the device current; make that first call before any stream capture.
+ *   The call never calls cudaMalloc, cudaFree or any allocating routine.
+ * Sharing: all calls share the one array, and it keeps the last call's
+ *   contents (each call overwrites every partial sum it reads, so nothing
+ *   needs clearing); two calls whose work overlaps on the GPU (on different
+ *   streams, say) race on it and must be ordered by the caller.
+ * Errors: QT_ERR_ARG (NULL pointer, unknown dtype), QT_ERR_RANGE (count),
+ *   QT_ERR_CUDA (address lookup or launch failed); the message is in
+ *   qt_last_error(NULL). */
+#define QT_NORM_STATIC_MAX_AMPS ((uint64_t)1 << 34)
+#define QT_NORM_STATIC_SCRATCH_BYTES 9728
+qt_status qt_norm_static(const void* amps_device, uint64_t count, int32_t dtype, double* out_device,
+                         void* cuda_stream);
+
 /* Options (value semantics):
  *   "ckpt_interval"  levels per checkpoint segment (>= 1; default 4)
  *   "fusion"         0: one gate per pass; 1: tile fusion (default)

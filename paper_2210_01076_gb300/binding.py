@@ -44,8 +44,8 @@ class qt_update_stats(ctypes.Structure):
 
 EXPORTED = ["qt_create", "qt_destroy", "qt_num_levels", "qt_num_gates", "qt_insert_level", "qt_remove_level",
             "qt_insert_gate", "qt_remove_gate", "qt_replace_gate", "qt_update_state", "qt_read_amplitudes",
-            "qt_read_amplitudes_device", "qt_norm", "qt_set_option", "qt_set_stream", "qt_num_segments",
-            "qt_segment_info", "qt_last_error"]
+            "qt_read_amplitudes_device", "qt_norm", "qt_norm_static", "qt_set_option", "qt_set_stream",
+            "qt_num_segments", "qt_segment_info", "qt_last_error"]
 
 
 class QtError(RuntimeError):
@@ -82,6 +82,7 @@ def load(path: str = LIB_PATH):
         "qt_read_amplitudes": [P, u64, u64, P],
         "qt_read_amplitudes_device": [P, u64, u64, P],
         "qt_norm": [P, ctypes.POINTER(ctypes.c_double)],
+        "qt_norm_static": [P, u64, i32, P, P],
         "qt_set_option": [P, ctypes.c_char_p, i64],
         "qt_set_stream": [P, P],
         "qt_num_segments": [P, ctypes.POINTER(i32)],
@@ -196,6 +197,13 @@ def qt_norm(h) -> float:
     v = ctypes.c_double()
     _check(h, load().qt_norm(h, ctypes.byref(v)))
     return v.value
+
+
+def qt_norm_static(amps_device_ptr: int, count: int, dtype: int, out_device_ptr: int, stream_ptr: int = 0):
+    """Norm of caller-held device amplitudes into a caller-held device double;
+    allocates nothing (see include/qtask.h)."""
+    _check(None, load().qt_norm_static(ctypes.c_void_p(amps_device_ptr), count, dtype,
+                                       ctypes.c_void_p(out_device_ptr), ctypes.c_void_p(stream_ptr or 0)))
 
 
 def qt_set_option(h, key: str, value: int):

@@ -35,6 +35,11 @@ using namespace qt;
 
 namespace {
 thread_local std::string g_create_error;
+}  // namespace
+
+void qt::set_thread_error(const std::string& msg) { g_create_error = msg; }
+
+namespace {
 
 int tile_low_default(int dtype) { return dtype == QT_C64 ? 7 : 6; }
 

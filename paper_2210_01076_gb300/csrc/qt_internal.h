@@ -190,6 +190,8 @@ int launch_read_convert(int dtype, void* dst, const void* state, uint64_t first,
 int launch_norm(int dtype, const void* state, uint64_t namps, double* partials, int npartials, double* out_dev,
                 void* stream);
 int norm_partials_needed(uint64_t namps);
+// Message for qt_last_error(NULL) on this thread.
+void set_thread_error(const std::string& msg);
 size_t bytes_per_amp(int dtype);
 // Encode a host op for the device (matrix entries in the dtype's arithmetic).
 void encode_matrix(int dtype, const HostOp& op, DevOp* out);
