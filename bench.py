@@ -59,7 +59,7 @@ def measured_peak():
 
 def kernel_source_hash():
     h = hashlib.sha256()
-    for f in ("qt_kernels.cu", "qt_internal.h"):
+    for f in ("qt_kernels.cu", "qt_pass_reg.cu", "qt_arith.cuh", "qt_internal.h"):
         with open(os.path.join(ROOT, "paper_2210_01076_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -144,6 +144,37 @@ def make_workload(seed, rounds):
     return levels, model, stream_model, edits
 
 
+# Arithmetic peaks from unit counts and the maximum SM clock: 152 SMs x 128
+# binary32 lanes x 2.07 GHz issue one binary32 instruction each per cycle;
+# binary64 FMA throughput is the measured 593 G/s of this GB300 (about 1.9 per
+# cycle per SM).  Float-float arithmetic is counted in binary32 instructions.
+SM_COUNT, SM_MAX_GHZ = 152, 2.07
+FP32_PEAK_TOPS = SM_COUNT * 128 * SM_MAX_GHZ / 1e3
+FP64_PEAK_TOPS = 0.593
+
+
+def roofline_pair(hbm_achieved, hbm_peak, peak_kind, alu_ops, kern_ms, dtype, traffic, launches, bytes_per_unit):
+    """The fused-pass kernel against both roofs; the primary entry is the
+    binding one (the larger fraction)."""
+    hbm = {"bound": "hbm", "achieved": hbm_achieved, "peak": hbm_peak, "unit": "GB/s",
+           "frac": (hbm_achieved / hbm_peak) if hbm_achieved else None, "peak_source": peak_kind,
+           "traffic": traffic, "bytes_per_unit": bytes_per_unit}
+    alu_peak = FP64_PEAK_TOPS if dtype == "c128" else FP32_PEAK_TOPS
+    alu_ach = (alu_ops / (kern_ms * 1e-3) / 1e12) if kern_ms and kern_ms > 0 else None
+    alu = {"bound": "alu", "achieved": alu_ach, "peak": alu_peak,
+           "unit": "T binary64 ops/s" if dtype == "c128" else "T binary32 ops/s",
+           "frac": (alu_ach / alu_peak) if alu_ach else None,
+           "peak_source": "unit counts x max SM clock" if dtype != "c128" else "measured FP64 FMA rate",
+           "ops_per_unit": "float-float: 86 binary32 ops per amplitude for a complex 2x2, 38 for a real 2x2, "
+                           "diagonal or complex multiply" if dtype == "c128df" else "8 per complex 2x2 row, 4 real/mul"}
+    primary = alu if (alu["frac"] or 0) > (hbm["frac"] or 0) else hbm
+    other = hbm if primary is alu else alu
+    out = dict(primary)
+    out.update({"traffic": traffic, "kernel": "k_pass_reg / k_pass_tma (fused tile pass)", "kernel_ms_total": kern_ms,
+                "kernel_launches": launches, "other_roof": other})
+    return out
+
+
 def config_dict(world):
     return {"workload": WORKLOAD, "n_qubits": N_QUBITS, "gates": N_GATES, "log2_partition": LOG2_PART,
             "ckpt_interval_levels": CKPT, "edits_per_round": "1-5", "parallelism": f"replicas{world}",
@@ -225,6 +256,7 @@ def run_ours(args):
     launches = sum(s["launches"] for s in stats)
     kern_ms = sum(s["pass_kernel_ms"] for s in stats)
     kern_bytes = sum(s["pass_kernel_bytes"] for s in stats)
+    alu_ops = sum(s["pass_kernel_alu_ops"] for s in stats)
     kern_launches = sum(s["pass_kernel_launches"] for s in stats)
     t_max = elapsed_ms
     amp_all = amp
@@ -319,11 +351,8 @@ def run_ours(args):
             "speedup_vs_full_p50": (pctl(fulls, 50) / pctl(inc_lat, 50)) if inc_lat else None,
             "accuracy": accuracy,
             "gpu_launches": launches,
-            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": (achieved / peak) if achieved else None, "peak_source": peak_kind,
-                         "traffic": traffic_per_launch, "kernel": "k_pass<ArDF> (fused tile pass)",
-                         "bytes_per_unit": "32 B per amplitude per pass (read + write of 16 B)",
-                         "kernel_ms_total": kern_ms, "kernel_launches": kern_launches},
+            "roofline": roofline_pair(achieved, peak, peak_kind, alu_ops, kern_ms, "c128df", traffic_per_launch,
+                                      kern_launches, "32 B per amplitude per pass (read + write of 16 B)"),
             "e2e": {"value": e2e_val, "unit": "amp-updates/s", "h2d_bytes_per_step": e2e_h2d / max(e2e_rounds, 1),
                     "d2h_bytes_per_step": (1 << N_QUBITS) * 16, "steps": e2e_rounds,
                     "note": "edits in, qt_update_state, whole state read to pinned host memory, each step"},
@@ -360,6 +389,71 @@ def cpu_baseline(levels, budget_s=15.0, gates_cap=None):
 
 
 # ------------------------------------------------------------- reference --
+
+def run_deep30(args):
+    """The large deep-circuit configuration: n = 30, 2000 gates of QFT-style
+    H + controlled-phase ladders interleaved with U3/CZ layers, complex64 or
+    complex128 (float-float); a full simulation, then single-gate edits in the
+    last 10 % of the levels, each followed by an incremental update.  Prints
+    its own JSON line (not the default benchmark)."""
+    import torch
+    from paper_2210_01076_gb300 import binding as B
+    from paper_2210_01076_gb300 import build as qbuild
+    from paper_2210_01076_gb300 import workloads as W
+    qbuild.build()
+    B.load()
+    n, ngates, p = 30, 2000, 18
+    dtype = args.dtype
+    levels = W.qft_like_circuit(n, ngates, seed=7)
+    stream = torch.cuda.Stream()
+    c = B.Circuit(n, dtype, p)
+    c.set_stream(stream.cuda_stream)
+    ckpt = args.deep_ckpt
+    c.set_option("ckpt_interval", ckpt)
+    for kv in args.option:
+        k, v = kv.split("=")
+        c.set_option(k, int(v))
+    ids = c.load_levels(levels)
+    c.update_state()
+    c.set_option("kernel_timing", 1)
+    fulls = [c.update_state(force_full=True) for _ in range(2)]
+    c.set_option("kernel_timing", 0)
+    full = fulls[-1]
+    rng = np.random.default_rng(11)
+    L = len(levels)
+    inc = []
+    for _ in range(args.steps):
+        lvl = int(rng.integers(int(0.9 * L), L))
+        if not ids[lvl]:
+            continue
+        k = int(rng.integers(len(ids[lvl])))
+        g = levels[lvl][k]
+        ng = W.make_gate("rz", [g.qubits[0]], [float(rng.normal(0.0, 0.1))]) if len(g.qubits) == 1 else g
+        ids[lvl][k] = c.replace_gate(lvl, ids[lvl][k], ng)
+        levels[lvl][k] = ng
+        inc.append(c.update_state())
+    norm = c.norm()
+    peak, peak_kind = measured_peak()
+    kb, km = full["pass_kernel_bytes"], full["pass_kernel_ms"]
+    achieved = kb / (km * 1e-3) / 1e9 if km > 0 else None
+    bpa = 8 if dtype == "c64" else 16
+    line = {
+        "metric": "amplitude-updates/s", "workload": "deep30",
+        "value": full["amp_updates"] / (full["gpu_ms"] * 1e-3), "unit": "amp-updates/s",
+        "dtype": {"c64": "c64 (fp32)", "c128df": "c128 (float-float)", "c128": "c128 (fp64)"}[dtype],
+        "config": {"workload": "QFT-like n=30, 2000 gates, partitions 2^18", "ckpt_interval_levels": ckpt,
+                   "levels": L, "segments": full["segments_total"], "passes": full["passes_total"]},
+        "full_sim_ms": full["gpu_ms"], "hbm_gbs": full["hbm_bytes"] / (full["gpu_ms"] * 1e-3) / 1e9,
+        "incremental_latency_ms": {"p50": pctl([s["gpu_ms"] for s in inc], 50),
+                                   "p99": pctl([s["gpu_ms"] for s in inc], 99)},
+        "clean_fraction_mean": float(np.mean([s["clean_fraction"] for s in inc])) if inc else None,
+        "norm": norm,
+        "roofline": roofline_pair(achieved, peak, peak_kind, full["pass_kernel_alu_ops"], km, dtype, None,
+                                  full["pass_kernel_launches"], f"{2 * bpa} B per amplitude per pass"),
+    }
+    print(json.dumps(line), flush=True)
+    c.close()
+
 
 def run_reference(args):
     rank, world, _ = rank_info()
@@ -413,12 +507,17 @@ def main():
     ap.add_argument("--n-qubits", type=int, default=N_QUBITS, help="smaller cases for profiling only")
     ap.add_argument("--ckpt", type=int, default=CKPT, help="levels per checkpoint segment")
     ap.add_argument("--option", action="append", default=[], help="extra qt_set_option key=value")
+    ap.add_argument("--workload", default="incremental24", choices=["incremental24", "deep30"])
+    ap.add_argument("--dtype", default="c128df", choices=["c128df", "c64", "c128"], help="deep30 only")
+    ap.add_argument("--deep-ckpt", type=int, default=48, help="deep30: levels per checkpoint segment")
     args = ap.parse_args()
     N_QUBITS, CKPT = args.n_qubits, args.ckpt
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "deep30":
+        run_deep30(args)
     else:
         run_ours(args)
 

@@ -114,6 +114,8 @@ typedef struct {
     int32_t reserved;
     uint64_t pass_kernel_bytes;  /* algorithmic bytes of those launches */
     uint64_t h2d_bytes;          /* host-to-device bytes uploaded (fused ops and worklists) */
+    uint64_t pass_kernel_alu_ops; /* algorithmic floating-point ops of the timed fused-pass launches
+                                     (binary32 ops for QT_C64 and QT_C128_DF, binary64 for QT_C128) */
 } qt_update_stats;
 
 /* Create an empty circuit (no levels) whose state is |0...0>.
@@ -170,6 +172,19 @@ qt_status qt_read_amplitudes_device(const qt_circuit* c, uint64_t first, uint64_
  * FP64-class accuracy for every dtype (float-float partial sums, FP64 tree). */
 qt_status qt_norm(const qt_circuit* c, double* out);
 
+/* Fidelity |<a|b>|^2 / (<a|a> <b|b>) of the current states of two circuits
+ * with the same qubit count (any dtypes; a complex64 result against a
+ * complex128 one measures the complex64 drift).  Both must be readable (no
+ * pending edits).  FP64-class reduction (float-float partial sums, binary64
+ * tree).  Runs on a's stream after waiting for b's. */
+qt_status qt_fidelity(const qt_circuit* a, const qt_circuit* b, double* out);
+
+/* Marginal probabilities of the k <= 10 qubits qubits[0..k-1] in the current
+ * state: out[v] (2^k doubles, host memory) = sum of |alpha_b|^2 over the
+ * indices b whose bit qubits[j] equals bit j of v (squared amplitudes are
+ * the probabilities of the basis states, Section II-A).  FP64-class. */
+qt_status qt_probabilities(const qt_circuit* c, int32_t k, const int32_t* qubits, double* out);
+
 /* qt_norm_static -- the norm of amplitudes the caller holds in device memory,
  * computed without allocating anything.  (The paper has no counterpart: this
  * entry point serves callers that cannot let a library call cudaMalloc, such
@@ -209,6 +224,13 @@ qt_status qt_norm_static(const void* amps_device, uint64_t count, int32_t dtype,
  *   "tile_high"      max qubits at or above the tile's low bits per pass (0..7)
  *   "mem_limit"      device-memory budget in bytes for state + checkpoints (0 = none)
  *   "kernel_timing"  1: time every fused-pass kernel with CUDA events (stats)
+ *   "tma"            1: persistent register kernel that stages the next tile with
+ *                    bulk copies (cp.async.bulk + mbarrier, bounded waits: a wait
+ *                    that expires makes qt_update_state return QT_ERR_TIMEOUT);
+ *                    0 (default): one CTA per tile
+ *   "test_stall_staging"  1 (with "tma" = 1): the staging copies are withheld, so
+ *                    the kernel's bounded wait expires after 1 s and the update
+ *                    returns QT_ERR_TIMEOUT; a failure-detection test hook
  *   "reg_kernel"     1: register-resident pass kernel for tiles of 2^7 amplitudes or more
  *                    (default); 0: shared-memory pass kernel for every tile
  *   "dry_run"        1: qt_update_state plans and tracks but launches nothing and

@@ -39,13 +39,14 @@ class qt_update_stats(ctypes.Structure):
                 ("amp_updates", ctypes.c_uint64), ("hbm_bytes", ctypes.c_uint64), ("host_ms", ctypes.c_double),
                 ("gpu_ms", ctypes.c_double), ("pass_kernel_ms", ctypes.c_double),
                 ("pass_kernel_launches", ctypes.c_int32), ("reserved", ctypes.c_int32),
-                ("pass_kernel_bytes", ctypes.c_uint64), ("h2d_bytes", ctypes.c_uint64)]
+                ("pass_kernel_bytes", ctypes.c_uint64), ("h2d_bytes", ctypes.c_uint64),
+                ("pass_kernel_alu_ops", ctypes.c_uint64)]
 
 
 EXPORTED = ["qt_create", "qt_destroy", "qt_num_levels", "qt_num_gates", "qt_insert_level", "qt_remove_level",
             "qt_insert_gate", "qt_remove_gate", "qt_replace_gate", "qt_update_state", "qt_read_amplitudes",
-            "qt_read_amplitudes_device", "qt_norm", "qt_norm_static", "qt_set_option", "qt_set_stream",
-            "qt_num_segments", "qt_segment_info", "qt_last_error"]
+            "qt_read_amplitudes_device", "qt_norm", "qt_norm_static", "qt_fidelity", "qt_probabilities",
+            "qt_set_option", "qt_set_stream", "qt_num_segments", "qt_segment_info", "qt_last_error"]
 
 
 class QtError(RuntimeError):
@@ -83,6 +84,8 @@ def load(path: str = LIB_PATH):
         "qt_read_amplitudes_device": [P, u64, u64, P],
         "qt_norm": [P, ctypes.POINTER(ctypes.c_double)],
         "qt_norm_static": [P, u64, i32, P, P],
+        "qt_fidelity": [P, P, ctypes.POINTER(ctypes.c_double)],
+        "qt_probabilities": [P, i32, ctypes.POINTER(i32), ctypes.POINTER(ctypes.c_double)],
         "qt_set_option": [P, ctypes.c_char_p, i64],
         "qt_set_stream": [P, P],
         "qt_num_segments": [P, ctypes.POINTER(i32)],
@@ -199,6 +202,20 @@ def qt_norm(h) -> float:
     return v.value
 
 
+def qt_fidelity(ha, hb) -> float:
+    v = ctypes.c_double()
+    _check(ha, load().qt_fidelity(ha, hb, ctypes.byref(v)))
+    return v.value
+
+
+def qt_probabilities(h, qubits) -> np.ndarray:
+    k = len(qubits)
+    q = (ctypes.c_int32 * max(k, 1))(*[int(x) for x in qubits])
+    out = np.zeros(1 << k, np.float64)
+    _check(h, load().qt_probabilities(h, k, q, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
+    return out
+
+
 def qt_norm_static(amps_device_ptr: int, count: int, dtype: int, out_device_ptr: int, stream_ptr: int = 0):
     """Norm of caller-held device amplitudes into a caller-held device double;
     allocates nothing (see include/qtask.h)."""
@@ -310,6 +327,12 @@ class Circuit:
 
     def norm(self) -> float:
         return qt_norm(self.h)
+
+    def fidelity(self, other: "Circuit") -> float:
+        return qt_fidelity(self.h, other.h)
+
+    def probabilities(self, qubits) -> np.ndarray:
+        return qt_probabilities(self.h, qubits)
 
     def num_segments(self) -> int:
         return qt_num_segments(self.h)

@@ -54,7 +54,28 @@ struct Launch {
     bool out_of_place;
     uint64_t parts_processed;
     int ngates;
+    double alu_per_amp;  // algorithmic arithmetic ops per amplitude of the pass
 };
+
+// Floating-point operations per amplitude that an op's arithmetic needs (the
+// formulas of qt_arith.cuh): float-float -- a 4-term dot product is 43 binary32
+// ops, a 2-term one 19, two per complex amplitude; binary32 / binary64 -- a
+// complex 2x2 row is 8 ops per amplitude, a real row, a complex multiply 4.
+// Phases count only the amplitudes whose condition bits are all 1;
+// permutations and exact phases (-1, +-i) need no arithmetic.
+double op_alu_per_amp(int dtype, const HostOp& op) {
+    const bool df = dtype == QT_C128_DF;
+    switch (op.kind) {
+        case OP_DENSE: return df ? 86.0 : 8.0;
+        case OP_REAL: case OP_DIAG: case OP_ANTI: return df ? 38.0 : 4.0;
+        case OP_PHASE: {
+            const bool exact = (op.m[0] == -1.0 && op.m[1] == 0.0) || (op.m[0] == 0.0 && (op.m[1] == 1.0 || op.m[1] == -1.0));
+            if (exact) return 0.0;
+            return (df ? 38.0 : 4.0) / double(uint64_t(1) << __builtin_popcountll(op.cmask));
+        }
+        default: return 0.0;
+    }
+}
 }  // namespace
 
 struct qt_circuit {
@@ -71,6 +92,8 @@ struct qt_circuit {
     bool kernel_timing = false;
     bool dry_run = false;
     bool reg_kernel = true;
+    bool tma = false;  // the bulk-copy staged persistent kernel measured slower than one CTA per tile
+    bool test_stall = false;
 
     // committed plan (matches the slabs when device_valid)
     bool have_plan = false;
@@ -99,9 +122,15 @@ struct qt_circuit {
     size_t h_wl_cap = 0;
     double* d_norm_partials = nullptr;
     double* d_norm_out = nullptr;
+    double* d_red = nullptr;   // reduction partial sums (fidelity, probabilities)
+    size_t d_red_cap = 0;      // in doubles
+    double* d_red_out = nullptr;
+    size_t d_red_out_cap = 0;
     int norm_cap = 0;
     void* d_read = nullptr;
     size_t d_read_cap = 0;
+    int* d_err = nullptr;  // set by a kernel whose bounded wait expired
+    int* h_err = nullptr;  // pinned copy read after each update
     cudaEvent_t ev_begin = nullptr, ev_end = nullptr;
     std::vector<cudaEvent_t> ev_pool;
 
@@ -154,7 +183,11 @@ void free_device(qt_circuit* c) {
     cudaFreeHost(c->h_wl);
     cudaFree(c->d_norm_partials);
     cudaFree(c->d_norm_out);
+    cudaFree(c->d_red);
+    cudaFree(c->d_red_out);
     cudaFree(c->d_read);
+    cudaFree(c->d_err);
+    cudaFreeHost(c->h_err);
     if (c->ev_begin) cudaEventDestroy(c->ev_begin);
     if (c->ev_end) cudaEventDestroy(c->ev_end);
     for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
@@ -189,6 +222,15 @@ qt_status ensure_device(qt_circuit* c) {
     c->slabs.push_back(s0);
     int rc = launch_init_zero_state(c->dtype, s0, c->namps(), c->stream);
     if (rc) return cuda_fail(c, rc, "init state");
+    if ((e = cudaMalloc(reinterpret_cast<void**>(&c->d_err), sizeof(int))) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(c, QT_ERR_OOM, "cudaMalloc of the error flag failed");
+    }
+    if ((e = cudaMallocHost(reinterpret_cast<void**>(&c->h_err), sizeof(int))) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(c, QT_ERR_OOM, "cudaMallocHost of the error flag failed");
+    }
+    *c->h_err = 0;
     c->device_ready = true;
     c->device_valid = false;
     return QT_OK;
@@ -460,6 +502,8 @@ qt_status do_update(qt_circuit* c, int force_full, qt_update_stats* stats) {
                 ln.ngroups = uint32_t(hwl.size() - ln.wl_offset);
             }
             ln.parts_processed = uint64_t(ln.ngroups) << __builtin_popcount(ps.M);
+            ln.alu_per_amp = 0.0;
+            for (const HostOp& o : ps.ops) ln.alu_per_amp += op_alu_per_amp(c->dtype, o);
             DevPass& dp = ln.dp;
             std::memset(&dp, 0, sizeof dp);
             dp.p = c->p;
@@ -479,6 +523,8 @@ qt_status do_update(qt_circuit* c, int force_full, qt_update_stats* stats) {
             pops.reserve(ps.ops.size());
             for (const HostOp& o : ps.ops) pops.push_back(encode_op(c->dtype, ps, o));
             if (c->reg_kernel) plan_register_layout(&dp, &pops);
+            dp.tma = (dp.reg_kernel && c->tma) ? 1 : 0;
+            dp.test_stall = c->test_stall ? 1 : 0;
             dp.nops = int32_t(pops.size());
             hops.insert(hops.end(), pops.begin(), pops.end());
             launches.push_back(ln);
@@ -519,6 +565,8 @@ qt_status do_update(qt_circuit* c, int force_full, qt_update_stats* stats) {
         cudaError_t e;
         c->device_valid = false;  // until the whole schedule has run
         if ((e = cudaEventRecord(c->ev_begin, c->stream)) != cudaSuccess) return cuda_fail(c, e, "event");
+        if ((e = cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream)) != cudaSuccess)
+            return cuda_fail(c, e, "error flag");
         if (!hops.empty() &&
             (e = cudaMemcpyAsync(c->d_ops, c->h_ops, hops.size() * sizeof(DevOp), cudaMemcpyHostToDevice,
                                  c->stream)) != cudaSuccess)
@@ -543,13 +591,18 @@ qt_status do_update(qt_circuit* c, int force_full, qt_update_stats* stats) {
                     cudaEventRecord(e0, c->stream);
                 }
                 rc = launch_pass(c->dtype, dst, ln.out_of_place ? src : dst, ln.dp, c->d_ops,
-                                 ln.null_worklist ? nullptr : c->d_wl + ln.wl_offset, ln.ngroups, c->stream);
+                                 ln.null_worklist ? nullptr : c->d_wl + ln.wl_offset, ln.ngroups, c->d_err,
+                                 c->stream);
                 if (c->kernel_timing) cudaEventRecord(e1, c->stream);
             }
             if (rc) return cuda_fail(c, rc, "kernel launch");
         }
         if ((e = cudaEventRecord(c->ev_end, c->stream)) != cudaSuccess) return cuda_fail(c, e, "event");
+        if ((e = cudaMemcpyAsync(c->h_err, c->d_err, sizeof(int), cudaMemcpyDeviceToHost, c->stream)) != cudaSuccess)
+            return cuda_fail(c, e, "error flag");
         if ((e = cudaStreamSynchronize(c->stream)) != cudaSuccess) return cuda_fail(c, e, "update_state");
+        if (*c->h_err != 0)
+            return fail(c, QT_ERR_TIMEOUT, "a bounded device wait expired (bulk copy did not complete in 1 s)");
         float ms = 0.0f;
         if (cudaEventElapsedTime(&ms, c->ev_begin, c->ev_end) == cudaSuccess) st.gpu_ms = ms;
         if (c->kernel_timing) {
@@ -563,6 +616,7 @@ qt_status do_update(qt_circuit* c, int force_full, qt_update_stats* stats) {
                 tot += km;
                 st.pass_kernel_launches += 1;
                 st.pass_kernel_bytes += 2 * bpa * ln.parts_processed * part_amps;
+                st.pass_kernel_alu_ops += uint64_t(ln.alu_per_amp * double(ln.parts_processed * part_amps));
             }
             st.pass_kernel_ms = tot;
         }
@@ -816,6 +870,66 @@ qt_status qt_read_amplitudes_device(const qt_circuit* cc, uint64_t first, uint64
     QT_GUARD_END(c)
 }
 
+qt_status qt_fidelity(const qt_circuit* ca, const qt_circuit* cb, double* out) {
+    qt_circuit* a = const_cast<qt_circuit*>(ca);
+    qt_circuit* b = const_cast<qt_circuit*>(cb);
+    if (!a) return QT_ERR_ARG;
+    if (!b || !out) return fail(a, QT_ERR_ARG, "b and out must not be NULL");
+    QT_GUARD_BEGIN
+    if (a->n != b->n) return fail(a, QT_ERR_ARG, "the two circuits have different qubit counts");
+    qt_status rs = check_readable(a);
+    if (rs != QT_OK) return rs;
+    rs = check_readable(b);
+    if (rs != QT_OK) return fail(a, rs, std::string("second circuit: ") + b->err);
+    cudaError_t e;
+    if (b->stream != a->stream && (e = cudaStreamSynchronize(b->stream)) != cudaSuccess)
+        return cuda_fail(a, e, "fidelity");
+    const int nb = reduce_blocks(a->namps());
+    if ((rs = grow_device(a, &a->d_red, &a->d_red_cap, size_t(4) * nb)) != QT_OK) return rs;
+    if ((rs = grow_device(a, &a->d_red_out, &a->d_red_out_cap, 4)) != QT_OK) return rs;
+    int rc = launch_fidelity(a->dtype, final_state(a), b->dtype, final_state(b), a->namps(), a->d_red, nb,
+                             a->d_red_out, a->stream);
+    if (rc) return cuda_fail(a, rc, "fidelity");
+    double h[4];
+    if ((e = cudaMemcpyAsync(h, a->d_red_out, sizeof h, cudaMemcpyDeviceToHost, a->stream)) != cudaSuccess)
+        return cuda_fail(a, e, "fidelity");
+    if ((e = cudaStreamSynchronize(a->stream)) != cudaSuccess) return cuda_fail(a, e, "fidelity");
+    if (!(h[2] > 0.0) || !(h[3] > 0.0)) return fail(a, QT_ERR_ARG, "a state has zero norm");
+    *out = (h[0] * h[0] + h[1] * h[1]) / (h[2] * h[3]);
+    return QT_OK;
+    QT_GUARD_END(a)
+}
+
+qt_status qt_probabilities(const qt_circuit* cc, int32_t k, const int32_t* qubits, double* out) {
+    qt_circuit* c = const_cast<qt_circuit*>(cc);
+    if (!c) return QT_ERR_ARG;
+    if (!out || (k > 0 && !qubits)) return fail(c, QT_ERR_ARG, "NULL argument");
+    QT_GUARD_BEGIN
+    if (k < 0 || k > 10) return fail(c, QT_ERR_ARG, "k must be in [0, 10]");
+    QubitList ql;
+    ql.k = k;
+    uint64_t seen = 0;
+    for (int j = 0; j < k; ++j) {
+        if (qubits[j] < 0 || qubits[j] >= c->n || ((seen >> qubits[j]) & 1))
+            return fail(c, QT_ERR_ARG, "qubits must be distinct and in [0, n)");
+        seen |= uint64_t(1) << qubits[j];
+        ql.q[j] = qubits[j];
+    }
+    qt_status rs = check_readable(c);
+    if (rs != QT_OK) return rs;
+    const int nb = reduce_blocks(c->namps());
+    const size_t nbins = size_t(1) << k;
+    if ((rs = grow_device(c, &c->d_red, &c->d_red_cap, nbins * nb)) != QT_OK) return rs;
+    if ((rs = grow_device(c, &c->d_red_out, &c->d_red_out_cap, nbins)) != QT_OK) return rs;
+    int rc = launch_probabilities(c->dtype, final_state(c), c->namps(), ql, c->d_red, nb, c->d_red_out, c->stream);
+    if (rc) return cuda_fail(c, rc, "probabilities");
+    cudaError_t e = cudaMemcpyAsync(out, c->d_red_out, nbins * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "probabilities");
+    if ((e = cudaStreamSynchronize(c->stream)) != cudaSuccess) return cuda_fail(c, e, "probabilities");
+    return QT_OK;
+    QT_GUARD_END(c)
+}
+
 qt_status qt_norm(const qt_circuit* cc, double* out) {
     qt_circuit* c = const_cast<qt_circuit*>(cc);
     if (!c) return QT_ERR_ARG;
@@ -867,6 +981,10 @@ qt_status qt_set_option(qt_circuit* c, const char* key, int64_t value) {
         c->mem_limit = value;
     } else if (k == "kernel_timing") {
         c->kernel_timing = value != 0;
+    } else if (k == "tma") {
+        c->tma = value != 0;
+    } else if (k == "test_stall_staging") {
+        c->test_stall = value != 0;
     } else if (k == "reg_kernel") {
         c->reg_kernel = value != 0;
     } else if (k == "dry_run") {

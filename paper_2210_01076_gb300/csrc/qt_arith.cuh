@@ -19,16 +19,25 @@ struct df {
     float hi, lo;
 };
 
+// Additions written as FMAs whose multiplier is a constant-memory 1.0 the
+// compiler cannot fold: fma(a, 1, b) is the same correctly rounded sum as
+// a + b, but it issues on the FMA pipe, which on this GPU has twice the
+// binary32 rate of the pipe that takes plain additions (ncu pipe counters of
+// the float-float kernels showed the addition pipe saturating first).
+__constant__ float kOneC = 1.0f;
+__device__ __forceinline__ float fadd(float a, float b) { return __fmaf_rn(a, kOneC, b); }
+__device__ __forceinline__ float fsub(float a, float b) { return __fmaf_rn(b, -kOneC, a); }
+
 __device__ __forceinline__ df two_sum(float a, float b) {
-    float s = __fadd_rn(a, b);
-    float bb = __fsub_rn(s, a);
-    float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+    float s = fadd(a, b);
+    float bb = fsub(s, a);
+    float e = fadd(fsub(a, fsub(s, bb)), fsub(b, bb));
     return {s, e};
 }
 
 __device__ __forceinline__ df fast_two_sum(float a, float b) {
-    float s = __fadd_rn(a, b);
-    float e = __fsub_rn(b, __fsub_rn(s, a));
+    float s = fadd(a, b);
+    float e = fsub(b, fsub(s, a));
     return {s, e};
 }
 
@@ -52,7 +61,7 @@ __device__ __forceinline__ df df_dot(const df (&a)[K], const df (&b)[K]) {
         ek = __fmaf_rn(a[k].lo, b[k].hi, ek);
         df t = two_sum(s, pk);
         s = t.hi;
-        err = __fadd_rn(err, __fadd_rn(t.lo, ek));
+        err = fadd(err, fadd(t.lo, ek));
     }
     return fast_two_sum(s, err);
 }

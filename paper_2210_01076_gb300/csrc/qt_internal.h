@@ -172,6 +172,8 @@ struct DevPass {
     int32_t reg_kernel;    // 1: register kernel with the initial layout below
     int32_t nreg, nwarp;   // register-index bits and warp bits (lane bits = 5)
     int32_t layout[8];     // tile bit of register bit k (k < nreg), then of warp bit w
+    int32_t tma;           // 1: persistent register kernel with bulk-copy (TMA) staging
+    int32_t test_stall;    // 1: withhold the staging copies so the bounded wait expires (test hook)
 };
 
 // Register-kernel layout planning for one pass (host): fills the initial
@@ -179,10 +181,12 @@ struct DevPass {
 void plan_register_layout(DevPass* dp, std::vector<DevOp>* ops);
 
 // Kernel launchers (qt_kernels.cu).  Return a cudaError_t as int.
+// err: device int set to 1 when a bounded wait of the TMA-staged kernel
+// expires (may be null: that kernel is then not used).
 int launch_pass(int dtype, void* dst, const void* src, const DevPass& dp, const DevOp* ops,
-                const uint32_t* worklist, uint32_t ngroups, void* stream);
+                const uint32_t* worklist, uint32_t ngroups, int* err, void* stream);
 int launch_pass_reg(int dtype, void* dst, const void* src, const DevPass& dp, const DevOp* ops,
-                    const uint32_t* worklist, uint32_t ngroups, void* stream);
+                    const uint32_t* worklist, uint32_t ngroups, int* err, void* stream);
 int launch_copy_parts(int dtype, void* dst, const void* src, int p, const uint32_t* parts, uint32_t nparts,
                       void* stream);
 int launch_init_zero_state(int dtype, void* state, uint64_t namps, void* stream);
@@ -192,6 +196,20 @@ int launch_norm(int dtype, const void* state, uint64_t namps, double* partials, 
 int norm_partials_needed(uint64_t namps);
 // Message for qt_last_error(NULL) on this thread.
 void set_thread_error(const std::string& msg);
+
+// Reductions (qt_reduce.cu).
+struct QubitList {
+    int32_t k;       // number of qubits (<= 10)
+    int32_t q[10];   // bit j of a bin is bit q[j] of the amplitude index
+};
+int reduce_blocks(uint64_t n);
+// out4 (device) receives Re<a|b>, Im<a|b>, <a|a>, <b|b>; partials: 4 per block.
+int launch_fidelity(int da, const void* a, int db, const void* b, uint64_t n, double* partials, int nblocks,
+                    double* out4, void* stream);
+// out (device, 2^k doubles): probability of each value of the listed qubits;
+// partials: 2^k per block.
+int launch_probabilities(int dtype, const void* s, uint64_t n, const QubitList& ql, double* partials, int nblocks,
+                         double* out, void* stream);
 size_t bytes_per_amp(int dtype);
 // Encode a host op for the device (matrix entries in the dtype's arithmetic).
 void encode_matrix(int dtype, const HostOp& op, DevOp* out);

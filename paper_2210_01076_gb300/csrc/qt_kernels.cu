@@ -221,8 +221,8 @@ int launch_pass_t(void* dst, const void* src, const DevPass& dp, const DevOp* op
 }
 
 int launch_pass(int dtype, void* dst, const void* src, const DevPass& dp, const DevOp* ops, const uint32_t* worklist,
-                uint32_t ngroups, void* stream) {
-    if (dp.reg_kernel) return launch_pass_reg(dtype, dst, src, dp, ops, worklist, ngroups, stream);
+                uint32_t ngroups, int* err, void* stream) {
+    if (dp.reg_kernel) return launch_pass_reg(dtype, dst, src, dp, ops, worklist, ngroups, err, stream);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     switch (dtype) {
         case QT_C128: return launch_pass_t<ArF64>(dst, src, dp, ops, worklist, ngroups, st);

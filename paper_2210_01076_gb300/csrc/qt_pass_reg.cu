@@ -213,47 +213,50 @@ struct RegOps {
         }
     }
 
+    // multiply the amplitudes whose condition bits are all 1 by the phase;
+    // registers that cannot qualify are skipped at compile time when the
+    // condition has at most one register bit
+    template <class F>
+    static __device__ __forceinline__ void masked(cx (&x)[R], uint32_t cmr, F&& f) {
+        if (cmr == 0) {
+#pragma unroll
+            for (int r = 0; r < R; ++r) x[r] = f(x[r]);
+        } else if ((cmr & (cmr - 1)) == 0) {
+            dispatch_k<RB>(__ffs(cmr) - 1, [&](auto kc) {
+                constexpr int K = decltype(kc)::value;
+#pragma unroll
+                for (int r = 0; r < R; ++r)
+                    if ((r >> K) & 1) x[r] = f(x[r]);
+            });
+        } else {
+#pragma unroll
+            for (int r = 0; r < R; ++r)
+                if ((uint32_t(r) & cmr) == cmr) x[r] = f(x[r]);
+        }
+    }
+
     static __device__ __forceinline__ void phase(cx (&x)[R], const DevOp* op, bool thr_ok, uint32_t cmr) {
+        if (!thr_ok) return;  // a condition bit held by the lane or warp index is 0
         const int sub = op->sub;
         if (sub == PH_NEG) {
-#pragma unroll
-            for (int r = 0; r < R; ++r)
-                if (thr_ok && (uint32_t(r) & cmr) == cmr) x[r] = A::neg(x[r]);
+            masked(x, cmr, [](cx v) { return A::neg(v); });
         } else if (sub == PH_POS_I) {
-#pragma unroll
-            for (int r = 0; r < R; ++r)
-                if (thr_ok && (uint32_t(r) & cmr) == cmr) x[r] = A::mul_i(x[r]);
+            masked(x, cmr, [](cx v) { return A::mul_i(v); });
         } else if (sub == PH_NEG_I) {
-#pragma unroll
-            for (int r = 0; r < R; ++r)
-                if (thr_ok && (uint32_t(r) & cmr) == cmr) x[r] = A::mul_negi(x[r]);
+            masked(x, cmr, [](cx v) { return A::mul_negi(v); });
         } else {
             const cx f = A::matp(op, 0);
-#pragma unroll
-            for (int r = 0; r < R; ++r) {
-                if (!(thr_ok && (uint32_t(r) & cmr) == cmr)) continue;
-                x[r] = A::mul(f, x[r]);
-            }
+            masked(x, cmr, [&](cx v) { return A::mul(f, v); });
         }
     }
 };
 
-template <class A, int RB>
-__global__ void __launch_bounds__(256) k_pass_reg(typename A::amp_t* __restrict__ dst,
-                                                   const typename A::amp_t* __restrict__ src, const DevPass dp,
-                                                   const DevOp* __restrict__ ops,
-                                                   const uint32_t* __restrict__ worklist) {
-    using amp_t = typename A::amp_t;
-    using cx = typename A::cx;
-    using RO = RegOps<A, RB>;
-    constexpr int R = 1 << RB;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    amp_t* tile = reinterpret_cast<amp_t*>(smem_raw);
-    __shared__ uint64_t choff[1 << kMaxTileHigh];
-
-    const uint32_t lane = threadIdx.x & 31u, wid = threadIdx.x >> 5;
-    const uint32_t gi = blockIdx.x >> dp.tpg_log2;
-    const uint32_t tau = blockIdx.x & ((1u << dp.tpg_log2) - 1u);
+// Index of the first amplitude of tile t: the partition group base (from the
+// worklist, or the t-th group when the worklist is null) and the tile
+// counter deposited into the partition bits that are not tile bits.
+__device__ __forceinline__ uint64_t tile_base(const DevPass& dp, const uint32_t* __restrict__ worklist, uint32_t t) {
+    const uint32_t gi = t >> dp.tpg_log2;
+    const uint32_t tau = t & ((1u << dp.tpg_log2) - 1u);
     uint32_t g;
     if (worklist != nullptr) {
         g = worklist[gi];
@@ -276,7 +279,11 @@ __global__ void __launch_bounds__(256) k_pass_reg(typename A::amp_t* __restrict_
             xb = ((xb & ~lowm) << 1) | (xb & lowm);
         }
     }
-    const uint64_t base = (uint64_t(g) << dp.p) | xb;
+    return (uint64_t(g) << dp.p) | xb;
+}
+
+// Offsets of the tile's 2^nh contiguous runs (chunks) of 2^lt amplitudes.
+__device__ __forceinline__ void chunk_offsets(const DevPass& dp, uint64_t* choff) {
     for (uint32_t c = threadIdx.x; c < (1u << dp.nh); c += blockDim.x) {
         uint64_t off = 0;
 #pragma unroll
@@ -284,40 +291,47 @@ __global__ void __launch_bounds__(256) k_pass_reg(typename A::amp_t* __restrict_
             if (k < dp.nh && ((c >> k) & 1u)) off |= uint64_t(1) << dp.h[k];
         choff[c] = off;
     }
+}
 
-    // layout: register bit k <-> tile bit field5(rpos, k); warp bits in jw
-    uint32_t rpos = 0;
+// Tile-index offset of register r in the layout rpos.
+template <int RB>
+__device__ __forceinline__ uint32_t joff(uint32_t rpos, int r) {
+    uint32_t o = 0;
+#pragma unroll
+    for (int k = 0; k < RB; ++k)
+        if ((r >> k) & 1) o |= 1u << field5(rpos, k);
+    return o;
+}
+
+// Initial layout of the pass: register bits and the lane / warp part jw.
+template <int RB>
+__device__ __forceinline__ void init_layout(const DevPass& dp, uint32_t lane, uint32_t wid, uint32_t& rpos,
+                                            uint32_t& jw) {
+    rpos = 0;
 #pragma unroll
     for (int k = 0; k < RB; ++k) rpos |= uint32_t(dp.layout[k]) << (5 * k);
-    uint32_t jw = lane;
+    jw = lane;
 #pragma unroll
     for (int w = 0; w < 3; ++w)
         if (w < dp.nwarp && ((wid >> w) & 1u)) jw |= 1u << dp.layout[RB + w];
-    auto joff = [&](int r) {
-        uint32_t o = 0;
-#pragma unroll
-        for (int k = 0; k < RB; ++k)
-            if ((r >> k) & 1) o |= 1u << field5(rpos, k);
-        return o;
-    };
-    __syncthreads();
+}
 
-    const uint32_t lowmask = (1u << dp.lt) - 1u;
-    cx x[R];
-#pragma unroll
-    for (int r = 0; r < R; ++r) {
-        const uint32_t j = jw | joff(r);
-        x[r] = A::ld(src[base | choff[j >> dp.lt] | (j & lowmask)]);
-    }
-
-    const DevOp* pops = ops + dp.op_offset;
-    for (int oi = 0; oi < dp.nops; ++oi) {
+// Apply the pass's ops to the thread's registers x (layout rpos / jw, both
+// updated by OP_PERM and register renames).  `tile` is the shared-memory
+// buffer for layout changes.  Every thread of the CTA must call this.
+template <class A, int RB>
+__device__ __forceinline__ void run_ops(typename A::cx (&x)[1 << RB], const DevOp* __restrict__ pops, int nops,
+                                        uint64_t base, uint32_t lane, uint32_t wid, uint32_t& rpos, uint32_t& jw,
+                                        typename A::amp_t* tile) {
+    using RO = RegOps<A, RB>;
+    constexpr int R = 1 << RB;
+    for (int oi = 0; oi < nops; ++oi) {
         const DevOp* op = pops + oi;
         const int kind = op->kind;
         if (kind == OP_PERM) {
             __syncthreads();  // the previous layout change has been read by all
 #pragma unroll
-            for (int r = 0; r < R; ++r) tile[jw | joff(r)] = A::st(x[r]);
+            for (int r = 0; r < R; ++r) tile[jw | joff<RB>(rpos, r)] = A::st(x[r]);
             __syncthreads();
             rpos = 0;
 #pragma unroll
@@ -327,7 +341,7 @@ __global__ void __launch_bounds__(256) k_pass_reg(typename A::amp_t* __restrict_
             for (int w = 0; w < 3; ++w)
                 if (w < op->nwarp && ((wid >> w) & 1u)) jw |= 1u << op->perm[RB + w];
 #pragma unroll
-            for (int r = 0; r < R; ++r) x[r] = A::ld(tile[jw | joff(r)]);
+            for (int r = 0; r < R; ++r) x[r] = A::ld(tile[jw | joff<RB>(rpos, r)]);
             continue;
         }
         const int role0 = op->role0;
@@ -393,54 +407,222 @@ __global__ void __launch_bounds__(256) k_pass_reg(typename A::amp_t* __restrict_
                 break;
         }
     }
+}
 
+// One CTA per tile: load from HBM into registers, run the ops, store.
+template <class A, int RB>
+__global__ void __launch_bounds__(256) k_pass_reg(typename A::amp_t* __restrict__ dst,
+                                                   const typename A::amp_t* __restrict__ src, const DevPass dp,
+                                                   const DevOp* __restrict__ ops,
+                                                   const uint32_t* __restrict__ worklist) {
+    using amp_t = typename A::amp_t;
+    using cx = typename A::cx;
+    constexpr int R = 1 << RB;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    amp_t* tile = reinterpret_cast<amp_t*>(smem_raw);
+    __shared__ uint64_t choff[1 << kMaxTileHigh];
+    const uint32_t lane = threadIdx.x & 31u, wid = threadIdx.x >> 5;
+    const uint64_t base = tile_base(dp, worklist, blockIdx.x);
+    chunk_offsets(dp, choff);
+    uint32_t rpos, jw;
+    init_layout<RB>(dp, lane, wid, rpos, jw);
+    __syncthreads();
+    const uint32_t lowmask = (1u << dp.lt) - 1u;
+    cx x[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) {
-        const uint32_t j = jw | joff(r);
+        const uint32_t j = jw | joff<RB>(rpos, r);
+        x[r] = A::ld(src[base | choff[j >> dp.lt] | (j & lowmask)]);
+    }
+    run_ops<A, RB>(x, ops + dp.op_offset, dp.nops, base, lane, wid, rpos, jw, tile);
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const uint32_t j = jw | joff<RB>(rpos, r);
         dst[base | choff[j >> dp.lt] | (j & lowmask)] = A::st(x[r]);
+    }
+}
+
+// ----------------------------------------------------- TMA-staged variant --
+// A persistent CTA walks the launch's tiles with a stride of gridDim.x.  While
+// it computes tile i, the bulk-copy engine (cp.async.bulk, one copy per
+// contiguous chunk, completion counted on an mbarrier) brings tile i+1 into a
+// second shared-memory buffer, so HBM reads overlap the arithmetic.  Every
+// wait on the mbarrier is bounded (1 s of %globaltimer); on expiry the CTA
+// raises the error flag and returns, and the host reports QT_ERR_TIMEOUT.
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_fence_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+__device__ __forceinline__ uint64_t global_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = global_ns();
+    while (!mbar_try_wait(bar, parity))
+        if (global_ns() - t0 > 1000000000ull) return false;
+    return true;
+}
+
+__device__ __forceinline__ void bulk_g2s(void* dst_smem, const void* src_gmem, uint32_t bytes, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_addr(dst_smem)),
+        "l"(src_gmem), "r"(bytes), "r"(smem_addr(bar))
+        : "memory");
+}
+
+template <class A, int RB>
+__global__ void __launch_bounds__(256, (RB <= 3 ? 3 : 1)) k_pass_tma(typename A::amp_t* __restrict__ dst,
+                                                   const typename A::amp_t* __restrict__ src, const DevPass dp,
+                                                   const DevOp* __restrict__ ops,
+                                                   const uint32_t* __restrict__ worklist, uint32_t ntiles,
+                                                   int* __restrict__ err) {
+    using amp_t = typename A::amp_t;
+    using cx = typename A::cx;
+    constexpr int R = 1 << RB;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    const uint32_t tb = uint32_t(dp.lt + dp.nh);
+    amp_t* inbuf = reinterpret_cast<amp_t*>(smem_raw);  // staged tile, indexed by tile index
+    amp_t* tile = inbuf + (1u << tb);                   // layout changes
+    __shared__ uint64_t choff[1 << kMaxTileHigh];
+    __shared__ __align__(8) uint64_t bar;
+    const uint32_t lane = threadIdx.x & 31u, wid = threadIdx.x >> 5;
+    chunk_offsets(dp, choff);
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        mbar_fence_init();
+    }
+    __syncthreads();
+    const uint32_t nchunks = 1u << dp.nh;
+    const uint32_t chunk_bytes = uint32_t(sizeof(amp_t)) << dp.lt;
+    auto issue = [&](uint32_t t) {  // warp 0 stages tile t into inbuf
+        if (wid == 0 && !dp.test_stall) {
+            const uint64_t b = tile_base(dp, worklist, t);
+            if (lane == 0) mbar_arrive_expect_tx(&bar, chunk_bytes * nchunks);
+            __syncwarp();
+            for (uint32_t c = lane; c < nchunks; c += 32)
+                bulk_g2s(inbuf + (c << dp.lt), src + (b | choff[c]), chunk_bytes, &bar);
+        }
+    };
+    uint32_t t = blockIdx.x;
+    if (t < ntiles) issue(t);
+    uint32_t parity = 0;
+    const uint32_t lowmask = (1u << dp.lt) - 1u;
+    for (; t < ntiles; t += gridDim.x) {
+        const uint64_t base = tile_base(dp, worklist, t);
+        const bool ok = mbar_wait_bounded(&bar, parity);
+        if (__syncthreads_or(!ok)) {
+            if (threadIdx.x == 0) atomicExch(err, 1);
+            return;
+        }
+        parity ^= 1u;
+        uint32_t rpos, jw;
+        init_layout<RB>(dp, lane, wid, rpos, jw);
+        cx x[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) x[r] = A::ld(inbuf[jw | joff<RB>(rpos, r)]);
+        __syncthreads();  // inbuf is free: stage the next tile while computing this one
+        if (t + gridDim.x < ntiles) issue(t + gridDim.x);
+        run_ops<A, RB>(x, ops + dp.op_offset, dp.nops, base, lane, wid, rpos, jw, tile);
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const uint32_t j = jw | joff<RB>(rpos, r);
+            dst[base | choff[j >> dp.lt] | (j & lowmask)] = A::st(x[r]);
+        }
     }
 }
 
 template <class A, int RB>
 int launch_reg_t(void* dst, const void* src, const DevPass& dp, const DevOp* ops, const uint32_t* worklist,
-                 uint32_t ngroups, cudaStream_t st) {
+                 uint32_t ngroups, int* err, cudaStream_t st) {
     using amp_t = typename A::amp_t;
-    const size_t smem = sizeof(amp_t) << (dp.lt + dp.nh);
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaError_t e =
-            cudaFuncSetAttribute(k_pass_reg<A, RB>, cudaFuncAttributeMaxDynamicSharedMemorySize, 128 * 1024);
-        if (e != cudaSuccess) return int(e);
-        attr_set = true;
-    }
+    const size_t tile_bytes = sizeof(amp_t) << (dp.lt + dp.nh);
     const uint64_t nblocks = uint64_t(ngroups) << dp.tpg_log2;
     if (nblocks == 0) return 0;
     const unsigned threads = 32u << dp.nwarp;
-    if (nblocks > 0x7fffffffull || smem > 128 * 1024 || dp.nreg != RB) return int(cudaErrorInvalidConfiguration);
-    k_pass_reg<A, RB><<<unsigned(nblocks), threads, smem, st>>>(static_cast<amp_t*>(dst),
-                                                                static_cast<const amp_t*>(src), dp, ops, worklist);
+    if (nblocks > 0x7fffffffull || tile_bytes > 64 * 1024 || dp.nreg != RB) return int(cudaErrorInvalidConfiguration);
+    const bool tma = dp.tma && err != nullptr && (uint32_t(sizeof(amp_t)) << dp.lt) % 16 == 0;
+    if (!tma) {
+        static bool attr_set = false;
+        if (!attr_set) {
+            cudaError_t e =
+                cudaFuncSetAttribute(k_pass_reg<A, RB>, cudaFuncAttributeMaxDynamicSharedMemorySize, 128 * 1024);
+            if (e != cudaSuccess) return int(e);
+            attr_set = true;
+        }
+        k_pass_reg<A, RB><<<unsigned(nblocks), threads, tile_bytes, st>>>(
+            static_cast<amp_t*>(dst), static_cast<const amp_t*>(src), dp, ops, worklist);
+        return int(cudaGetLastError());
+    }
+    static bool tattr_set = false;
+    static int nsm = 0;
+    if (!tattr_set) {
+        cudaError_t e =
+            cudaFuncSetAttribute(k_pass_tma<A, RB>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
+        if (e != cudaSuccess) return int(e);
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+        tattr_set = true;
+    }
+    const size_t smem = 2 * tile_bytes;
+    int per_sm = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pass_tma<A, RB>, int(threads), smem);
+    if (e != cudaSuccess) return int(e);
+    if (per_sm < 1) per_sm = 1;
+    const uint64_t grid = std::min<uint64_t>(nblocks, uint64_t(nsm) * uint64_t(per_sm));
+    k_pass_tma<A, RB><<<unsigned(grid), threads, smem, st>>>(static_cast<amp_t*>(dst),
+                                                             static_cast<const amp_t*>(src), dp, ops, worklist,
+                                                             uint32_t(nblocks), err);
     return int(cudaGetLastError());
 }
 
 template <class A>
 int launch_reg_a(void* dst, const void* src, const DevPass& dp, const DevOp* ops, const uint32_t* worklist,
-                 uint32_t ngroups, cudaStream_t st) {
+                 uint32_t ngroups, int* err, cudaStream_t st) {
     switch (dp.nreg) {
-        case 2: return launch_reg_t<A, 2>(dst, src, dp, ops, worklist, ngroups, st);
-        case 3: return launch_reg_t<A, 3>(dst, src, dp, ops, worklist, ngroups, st);
-        case 4: return launch_reg_t<A, 4>(dst, src, dp, ops, worklist, ngroups, st);
-        case 5: return launch_reg_t<A, 5>(dst, src, dp, ops, worklist, ngroups, st);
+        case 2: return launch_reg_t<A, 2>(dst, src, dp, ops, worklist, ngroups, err, st);
+        case 3: return launch_reg_t<A, 3>(dst, src, dp, ops, worklist, ngroups, err, st);
+        case 4: return launch_reg_t<A, 4>(dst, src, dp, ops, worklist, ngroups, err, st);
+        case 5: return launch_reg_t<A, 5>(dst, src, dp, ops, worklist, ngroups, err, st);
         default: return int(cudaErrorInvalidConfiguration);
     }
 }
 
 int launch_pass_reg(int dtype, void* dst, const void* src, const DevPass& dp, const DevOp* ops,
-                    const uint32_t* worklist, uint32_t ngroups, void* stream) {
+                    const uint32_t* worklist, uint32_t ngroups, int* err, void* stream) {
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     switch (dtype) {
-        case QT_C128: return launch_reg_a<ArF64>(dst, src, dp, ops, worklist, ngroups, st);
-        case QT_C64: return launch_reg_a<ArF32>(dst, src, dp, ops, worklist, ngroups, st);
-        case QT_C128_DF: return launch_reg_a<ArDF>(dst, src, dp, ops, worklist, ngroups, st);
+        case QT_C128: return launch_reg_a<ArF64>(dst, src, dp, ops, worklist, ngroups, err, st);
+        case QT_C64: return launch_reg_a<ArF32>(dst, src, dp, ops, worklist, ngroups, err, st);
+        case QT_C128_DF: return launch_reg_a<ArDF>(dst, src, dp, ops, worklist, ngroups, err, st);
         default: return int(cudaErrorInvalidValue);
     }
 }

@@ -150,18 +150,19 @@ uint64_t op_qubits(const HostOp& op) {
 
 int popcount64(uint64_t x) { return __builtin_popcountll(x); }
 
-// Arithmetic per amplitude of an op in float-float (the costliest arithmetic;
-// the binary32 and binary64 kernels have the same proportions): a complex 2x2
-// is two 4-term dot products per amplitude, a real 2x2, a diagonal or an
-// anti-diagonal two 2-term ones, a general phase touches half the
-// amplitudes, exact phases (-1, +-i) and permutations only move data.
+// Instructions per amplitude of an op in float-float (the costliest
+// arithmetic; the binary32 and binary64 kernels have the same proportions): a
+// complex 2x2 is two 4-term dot products per amplitude, a real 2x2, a
+// diagonal, an anti-diagonal or a general phase two 2-term ones (a phase runs
+// predicated over all amplitudes of a thread), exact phases (-1, +-i) and
+// permutations only move data.
 int op_cost(const HostOp& op) {
     switch (op.kind) {
         case OP_DENSE: return 86;
         case OP_REAL: case OP_DIAG: case OP_ANTI: return 38;
         case OP_PHASE: {
             const bool exact = (op.m[0] == -1.0 && op.m[1] == 0.0) || (op.m[0] == 0.0 && std::fabs(op.m[1]) == 1.0);
-            return exact ? 1 : 19;
+            return exact ? 4 : 38;
         }
         default: return 1;
     }
@@ -225,16 +226,15 @@ bool lower_gate(const qt_gate& g, int n, std::vector<HostOp>* out, std::string* 
     }
     uint64_t cmask = 0;
     for (int k = 0; k < g.ncontrol; ++k) cmask |= uint64_t(1) << g.control[k];
-    if ((g.kind == QT_RX || g.kind == QT_U3) && cmask == 0) {
-        // A complex 2x2 costs about twice a real one; write these as a real
-        // rotation between two phases (exact for RX):
-        //   U3(t,p,l) = diag(1, e^{ip}) RY(t) diag(1, e^{il})
-        //   RX(t)     = diag(1, -i)     RY(t) diag(1, i)
+    if (g.kind == QT_RX && cmask == 0) {
+        // A complex 2x2 costs about twice a real one; RX is a real rotation
+        // between two exact phases (a multiply by +-i only moves data):
+        //   RX(t) = diag(1, -i) RY(t) diag(1, i)
         const double t = g.theta[0];
         const double c = std::cos(t / 2.0), s = std::sin(t / 2.0);
         const cd I(0.0, 1.0);
-        const cd first = g.kind == QT_RX ? I : std::polar(1.0, g.theta[2]);
-        const cd last = g.kind == QT_RX ? -I : std::polar(1.0, g.theta[1]);
+        const cd first = I;
+        const cd last = -I;
         M2 P1, RY, P2;
         P1.a[0] = 1.0; P1.a[1] = 0.0; P1.a[2] = 0.0; P1.a[3] = first;
         RY.a[0] = c; RY.a[1] = -s; RY.a[2] = s; RY.a[3] = c;

@@ -93,6 +93,87 @@ def test_random_circuit_config1_shape(dtype, fusion, tile_high, reg):
 
 
 @pytest.mark.parametrize("dtype", DTYPES)
+def test_tma_staged_kernel_parity_and_bit_identity(dtype):
+    """The persistent kernel that stages tiles with bulk copies (option tma)
+    against the oracle, and incremental against full on it."""
+    n, p = 14, 7
+    levels = W.random_circuit(n, 250, seed=17, p_multi=0.4)
+    c, ids = build_circuit(n, levels, dtype, p, tma=1, ckpt_interval=2)
+    c.update_state()
+    want = oracle.simulate(n, W.flatten(levels))
+    assert max_err(c.read_amplitudes(), want) <= TOL[dtype]
+    last = len(ids) - 3
+    c.remove_gate(last, ids[last][0])
+    c.update_state()
+    inc = c.read_amplitudes()
+    c.update_state(force_full=True)
+    assert np.array_equal(inc.view(np.uint8), c.read_amplitudes().view(np.uint8))
+
+
+def test_fidelity_and_probabilities():
+    n = 14
+    levels = W.random_circuit(n, 300, seed=23, p_multi=0.4)
+    want = oracle.simulate(n, W.flatten(levels))
+    cs = {dt: build_circuit(n, levels, dt, 8)[0] for dt in DTYPES}
+    for c in cs.values():
+        c.update_state()
+    got64 = cs["c64"].read_amplitudes().astype(np.complex128)
+    f = cs["c64"].fidelity(cs["c128df"])
+    assert abs(f - fidelity(got64, want)) <= 1e-9 and f >= 1 - 1e-6
+    assert abs(cs["c128df"].fidelity(cs["c128"]) - 1.0) <= 1e-12
+    assert abs(cs["c128"].fidelity(cs["c128df"]) - 1.0) <= 1e-12
+    probs = np.abs(want) ** 2
+    idx = np.arange(1 << n)
+    for qs in ([], [3], [0, 5, 13], [13, 2], list(range(10))):
+        ref = np.zeros(1 << len(qs))
+        v = np.zeros(1 << n, dtype=np.int64)
+        for j, q in enumerate(qs):
+            v |= ((idx >> q) & 1) << j
+        np.add.at(ref, v, probs)
+        for dt, c in cs.items():
+            tol = 1e-12 if dt != "c64" else 1e-6
+            assert np.max(np.abs(c.probabilities(qs) - ref)) <= tol, (dt, qs)
+    with pytest.raises(B.QtError):
+        cs["c64"].probabilities([1, 1])
+
+
+def test_complex64_drift_falls_back_to_complex128():
+    from paper_2210_01076_gb300.precision import AdaptiveCircuit
+    n = 12
+    levels = W.random_circuit(n, 400, seed=31, p_multi=0.4)
+    want = oracle.simulate(n, W.flatten(levels))
+    loose = AdaptiveCircuit(n, 8, drift_tol=1e-3)
+    loose.load_levels(levels)
+    loose.update_state()
+    assert loose.dtype == "c64" and loose.drift is not None and loose.drift <= 1e-3
+    assert max_err(loose.read_amplitudes(), want) <= 1e-5
+    strict = AdaptiveCircuit(n, 8, drift_tol=1e-12)
+    strict.load_levels(levels)
+    strict.update_state()
+    assert strict.dtype == "c128df" and strict.switched_at_update == 1
+    assert max_err(strict.read_amplitudes(), want) <= 1e-12
+    strict.insert_level(0)
+    strict.insert_gate(0, W.make_gate("h", [0]))
+    strict.update_state()
+    assert max_err(strict.read_amplitudes(), oracle.simulate(n, [W.make_gate("h", [0])] + W.flatten(levels))) <= 1e-12
+
+
+def test_bounded_wait_expiry_reports_timeout():
+    """Failure detection without a fault: the staging copies are withheld, the
+    kernel's bounded wait expires (1 s), the update reports QT_ERR_TIMEOUT, and
+    the context stays usable for the next update."""
+    n, p = 12, 8
+    levels = W.random_circuit(n, 60, seed=3)
+    c, _ = build_circuit(n, levels, "c128df", p, tma=1, test_stall_staging=1)
+    with pytest.raises(B.QtError) as e:
+        c.update_state()
+    assert e.value.status == B.QT_ERR_TIMEOUT
+    c.set_option("test_stall_staging", 0)
+    c.update_state()
+    assert max_err(c.read_amplitudes(), oracle.simulate(n, W.flatten(levels))) <= 1e-12
+
+
+@pytest.mark.parametrize("dtype", DTYPES)
 def test_qft_like_circuit(dtype):
     n, p = 13, 6
     levels = W.qft_like_circuit(n, 400, seed=5)
