@@ -455,6 +455,185 @@ def run_deep30(args):
     c.close()
 
 
+def run_serve(args):
+    """Served request stream: 64 resident circuits of 16-28 qubits (complex64,
+    300-1500 random gates), requests of 1-5 edits + an incremental update
+    arriving as a Poisson stream, device memory admitted against a 150 GB
+    budget including checkpoints.  Reports throughput and p50/p99 latency at
+    the offered 2000 req/s and at 70 % of the measured capacity."""
+    import threading
+    from paper_2210_01076_gb300 import binding as B
+    from paper_2210_01076_gb300 import build as qbuild
+    from paper_2210_01076_gb300 import workloads as W
+    qbuild.build()
+    B.load()
+    rng = np.random.default_rng(55)
+    ncirc = args.serve_circuits
+    circs, mirrors, ids, ns = [], [], [], []
+    for c in range(ncirc):
+        n = int(rng.integers(16, 29))
+        levels = W.random_circuit(n, int(rng.integers(300, 1501)), seed=5000 + c, p_multi=0.4)
+        circ = B.Circuit(n, "c64", min(n, 16))
+        circ.set_option("ckpt_interval", max(4, -(-len(levels) // 8)))  # at most ~9 checkpoints
+        ids.append(circ.load_levels(levels))
+        mirrors.append([list(lv) for lv in levels])
+        circs.append(circ)
+        ns.append(n)
+    budget = int(args.serve_budget_gb * 1e9)
+    srv = B.Server(workers=args.serve_workers, hbm_budget_bytes=budget)
+    slots = [srv.add_circuit(c) for c in circs]
+    t0 = time.perf_counter()
+    for t in [srv.submit(s, []) for s in slots]:
+        srv.wait(t)
+    warm_s = time.perf_counter() - t0
+    replaced = [set() for _ in range(ncirc)]
+
+    def make_request():
+        c = int(rng.integers(ncirc))
+        ops = []
+        for _ in range(int(rng.integers(1, 6))):
+            if rng.random() < 0.5:
+                lvl = int(rng.integers(len(mirrors[c]) + 1))
+                g = W.random_gate(rng, ns[c], 0.4)
+                ops += [("insert_level", lvl), ("insert", lvl, g)]
+                mirrors[c].insert(lvl, [g])
+                ids[c].insert(lvl, [None])
+            else:
+                cand = [(l, k) for l, lv in enumerate(ids[c]) for k, gid in enumerate(lv)
+                        if gid is not None and gid not in replaced[c]]
+                if not cand:
+                    continue
+                l, k = cand[int(rng.integers(len(cand)))]
+                q = list(mirrors[c][l][k].qubits)
+                same = [nm for nm in W.ALL_KINDS if sum(W.ARITY[nm][:2]) == len(q)]
+                nm = same[int(rng.integers(len(same)))]
+                ng = W.make_gate(nm, q, rng.uniform(0, 2 * np.pi, W.ARITY[nm][2]))
+                ops.append(("replace", l, ids[c][l][k], ng))
+                replaced[c].add(ids[c][l][k])
+                mirrors[c][l][k] = ng
+                ids[c][l][k] = None
+        return c, ops
+
+    def open_loop(rate, seconds):
+        arrivals = np.cumsum(rng.exponential(1.0 / rate, size=int(rate * seconds * 1.2) + 1))
+        arrivals = arrivals[arrivals < seconds]
+        reqs = [make_request() for _ in arrivals]
+        tickets, results = [], []
+        done = threading.Event()
+
+        def waiter():
+            k = 0
+            while k < len(arrivals):
+                while len(tickets) <= k:
+                    time.sleep(0.0005)
+                results.append(srv.wait(tickets[k]))
+                k += 1
+            done.set()
+        th = threading.Thread(target=waiter)
+        th.start()
+        start = time.perf_counter()
+        for (c, ops), at in zip(reqs, arrivals):
+            dt = start + at - time.perf_counter()
+            if dt > 0:
+                time.sleep(dt)
+            tickets.append(srv.submit(slots[c], ops))
+        th.join()
+        wall = time.perf_counter() - start
+        lat = [r["latency_ms"] for r in results]
+        amp = sum(r["stats"]["amp_updates"] for r in results)
+        return {"offered_req_s": rate, "window_s": seconds, "requests": len(results), "wall_s": wall,
+                "throughput_req_s": len(results) / wall, "amp_updates_per_s": amp / wall,
+                "latency_ms": {"p50": pctl(lat, 50), "p99": pctl(lat, 99)},
+                "queue_ms_p50": pctl([r["queue_ms"] for r in results], 50),
+                "service_ms_p50": pctl([r["service_ms"] for r in results], 50),
+                "errors": sum(1 for r in results if r["status"] != 0)}
+
+    # capacity: a closed burst
+    burst = [make_request() for _ in range(args.serve_burst)]
+    tb = time.perf_counter()
+    tickets = [srv.submit(slots[c], ops) for c, ops in burst]
+    res = [srv.wait(t) for t in tickets]
+    cap = len(res) / (time.perf_counter() - tb)
+    at_2k = open_loop(2000.0, args.serve_seconds)
+    at_70 = open_loop(0.7 * cap, args.serve_seconds)
+    info = srv.info()
+    srv.close()
+    line = {"metric": "served requests", "workload": "serve64", "dtype": "c64 (fp32)",
+            "config": {"circuits": ncirc, "qubits": "16-28", "gates": "300-1500", "edits_per_request": "1-5",
+                       "workers": args.serve_workers, "hbm_budget_gb": args.serve_budget_gb},
+            "warmup_full_sims_s": warm_s, "capacity_req_s": cap, "at_offered_2000": at_2k,
+            "at_70pct_capacity": at_70, "evictions": info["evictions"],
+            "resident_gb": info["resident_bytes"] / 1e9}
+    print(json.dumps(line), flush=True)
+    for c in circs:
+        c.close()
+
+
+def run_batch(args):
+    """Batched synthesis loop: 256 independent complex64 circuits, qubit
+    counts uniform in [10, 20], depths (ASAP levels) uniform in [50, 400],
+    simulated together in one persistent launch; then 10 rounds in which
+    every circuit gets one parameter edit (an RZ or RY angle moved by
+    N(0, 0.1)) and the batch re-runs (CUDA-graph replay)."""
+    from paper_2210_01076_gb300 import binding as B
+    from paper_2210_01076_gb300 import build as qbuild
+    from paper_2210_01076_gb300 import workloads as W
+    qbuild.build()
+    B.load()
+    rng = np.random.default_rng(404)
+    circs, levels, ids = [], [], []
+    for k in range(args.batch_circuits):
+        n = int(rng.integers(10, 21))
+        depth = int(rng.integers(50, 401))
+        gates, last = [], [-1] * n
+        while True:
+            g = W.random_gate(rng, n, 0.4)
+            lv = 1 + max(last[q] for q in g.qubits)
+            if lv >= depth:
+                break
+            for q in g.qubits:
+                last[q] = lv
+            gates.append(g)
+        lvls = W.asap_levels(n, gates)
+        c = B.Circuit(n, "c64", min(n, 16))
+        ids.append(c.load_levels(lvls))
+        levels.append([list(x) for x in lvls])
+        circs.append(c)
+    batch = B.Batch(circs)
+    first = batch.run()
+    capture = batch.run()
+    rounds = []
+    for _ in range(args.batch_rounds):
+        for k, c in enumerate(circs):
+            cand = [(l, j) for l, lv in enumerate(levels[k]) for j, g in enumerate(lv) if g.name in ("rz", "ry")]
+            if not cand:
+                continue
+            l, j = cand[int(rng.integers(len(cand)))]
+            g = levels[k][l][j]
+            ng = g._replace(params=(g.params[0] + float(rng.normal(0.0, 0.1)),))
+            ids[k][l][j] = c.replace_gate(l, ids[k][l][j], ng)
+            levels[k][l][j] = ng
+        rounds.append(batch.run())
+    # one circuit checked against the oracle after the last round
+    import oracle
+    k = int(np.argmin([c.n for c in circs]))
+    err = float(np.max(np.abs(batch.read_amplitudes(k).astype(np.complex128)
+                              - oracle.simulate(circs[k].n, W.flatten(levels[k])))))
+    ms = [r["gpu_ms"] for r in rounds]
+    amp = rounds[-1]["amp_updates"] if rounds else first["amp_updates"]
+    line = {"metric": "amplitude-updates/s", "workload": "batch256", "dtype": "c64 (fp32)",
+            "value": amp / (np.median(ms) * 1e-3), "unit": "amp-updates/s",
+            "config": {"circuits": len(circs), "qubits": "10-20", "depth": "50-400",
+                       "gates_total": int(sum(c.num_gates() for c in circs)), "passes": rounds[-1]["passes"],
+                       "tiles_per_launch": rounds[-1]["tiles"]},
+            "first_run_ms": first["gpu_ms"], "capture_run_ms": capture["gpu_ms"],
+            "round_ms": {"p50": pctl(ms, 50), "p99": pctl(ms, 99)},
+            "graph_replays": int(sum(r["graph_replayed"] for r in rounds)), "rounds": len(rounds),
+            "max_abs_err_vs_oracle_smallest_circuit": err}
+    print(json.dumps(line), flush=True)
+    batch.close()
+
+
 def run_reference(args):
     rank, world, _ = rank_info()
     if rank != 0:
@@ -507,7 +686,14 @@ def main():
     ap.add_argument("--n-qubits", type=int, default=N_QUBITS, help="smaller cases for profiling only")
     ap.add_argument("--ckpt", type=int, default=CKPT, help="levels per checkpoint segment")
     ap.add_argument("--option", action="append", default=[], help="extra qt_set_option key=value")
-    ap.add_argument("--workload", default="incremental24", choices=["incremental24", "deep30"])
+    ap.add_argument("--workload", default="incremental24", choices=["incremental24", "deep30", "serve", "batch"])
+    ap.add_argument("--batch-circuits", type=int, default=256)
+    ap.add_argument("--batch-rounds", type=int, default=10)
+    ap.add_argument("--serve-circuits", type=int, default=64)
+    ap.add_argument("--serve-workers", type=int, default=8)
+    ap.add_argument("--serve-budget-gb", type=float, default=150.0)
+    ap.add_argument("--serve-seconds", type=float, default=2.0)
+    ap.add_argument("--serve-burst", type=int, default=200)
     ap.add_argument("--dtype", default="c128df", choices=["c128df", "c64", "c128"], help="deep30 only")
     ap.add_argument("--deep-ckpt", type=int, default=48, help="deep30: levels per checkpoint segment")
     args = ap.parse_args()
@@ -518,6 +704,10 @@ def main():
         run_reference(args)
     elif args.workload == "deep30":
         run_deep30(args)
+    elif args.workload == "serve":
+        run_serve(args)
+    elif args.workload == "batch":
+        run_batch(args)
     else:
         run_ours(args)
 

@@ -256,6 +256,98 @@ qt_status qt_segment_info(const qt_circuit* c, int32_t seg, int32_t* first_level
  * c is NULL).  Valid until the next call on c. */
 const char* qt_last_error(const qt_circuit* c);
 
+/* Free the circuit's device memory (state, checkpoints, buffers) and keep
+ * its circuit; the next qt_update_state re-simulates in full. */
+qt_status qt_release_device(qt_circuit* c);
+
+/* Device bytes the circuit currently holds for its state and checkpoints. */
+qt_status qt_device_bytes(const qt_circuit* c, int64_t* out);
+
+/* ------------------------------------------------------------ batches ---
+ * Many small circuits (10 or more qubits each; tiles of 2^10-2^12
+ * amplitudes) simulated together in ONE persistent launch: the tiles of all
+ * circuits' passes are dequeued in wavefront order and each waits (bounded,
+ * 1 s; QT_ERR_TIMEOUT if it expires) only for the previous pass of its own
+ * circuit.  A run re-simulates every circuit in full from |0...0> with its
+ * current gates (edits are made on the circuits with the usual calls) into
+ * the batch's own device arena; the circuits' own states are untouched.
+ * From the second run with an unchanged structure the whole run is a CUDA
+ * graph replay; parameter edits (new angles) keep the structure. */
+typedef struct qt_batch qt_batch;
+
+typedef struct {
+    double gpu_ms;            /* device time of the run (CUDA events) */
+    int32_t circuits;
+    int32_t passes;           /* fused passes over all circuits */
+    int32_t tiles;            /* work items of the persistent launch */
+    int32_t graph_replayed;   /* 1: the run replayed the captured graph */
+    uint64_t amp_updates;     /* sum over circuits of gates x 2^n */
+} qt_batch_stats;
+
+/* All circuits must share one dtype.  The batch references the circuits
+ * (the caller keeps them alive and unchanged during qt_batch_run). */
+qt_status qt_batch_create(qt_circuit* const* circuits, int32_t count, qt_batch** out);
+qt_status qt_batch_run(qt_batch* b, qt_batch_stats* stats);
+/* Amplitudes of circuit `index` from the last run (format as qt_read_amplitudes). */
+qt_status qt_batch_read_amplitudes(const qt_batch* b, int32_t index, uint64_t first, uint64_t count,
+                                   void* host_dst);
+qt_status qt_batch_destroy(qt_batch* b);
+/* Message of the batch's last failed call. */
+const char* qt_batch_last_error(const qt_batch* b);
+
+/* ------------------------------------------------------------ serving ---
+ * A request is a short list of circuit edits followed by an incremental
+ * update of one circuit -- the paper's incremental iteration, Section IV-C.
+ * The server runs requests on `workers` host threads; every circuit has its
+ * own CUDA stream, so requests on different circuits overlap on the GPU, and
+ * a request arriving while others run starts as soon as a worker and device
+ * memory are free (continuous batching).  Device memory (state plus
+ * checkpoints of every resident circuit) is admitted against
+ * hbm_budget_bytes (0 = no budget): a request whose circuit is not resident
+ * and does not fit evicts idle circuits least-recently-used first
+ * (qt_release_device), or waits while other requests proceed.  Requests on
+ * one circuit run in submission order.  The caller keeps ownership of the
+ * circuits and must not call into a circuit while the server may use it. */
+typedef struct qt_server qt_server;
+
+typedef enum {
+    QT_EDIT_INSERT_LEVEL = 0, /* level */
+    QT_EDIT_INSERT_GATE = 1,  /* level, gate */
+    QT_EDIT_REMOVE_GATE = 2,  /* level, id */
+    QT_EDIT_REPLACE_GATE = 3, /* level, id, gate */
+    QT_EDIT_REMOVE_LEVEL = 4  /* level */
+} qt_edit_kind;
+
+typedef struct {
+    int32_t kind;
+    int32_t level;
+    qt_gate_id id;
+    qt_gate gate;
+} qt_edit;
+
+typedef struct {
+    int32_t status;          /* qt_status of the request */
+    int32_t circuit;         /* slot */
+    double queue_ms;         /* submit -> start (waiting for a worker, the circuit or memory) */
+    double service_ms;       /* start -> done */
+    double latency_ms;       /* submit -> done */
+    qt_update_stats stats;   /* of the request's qt_update_state */
+    int32_t n_new_ids;       /* ids created by the request's inserts and replaces, in order */
+    int32_t reserved;
+    qt_gate_id new_ids[8];
+} qt_request_result;
+
+qt_status qt_server_create(int32_t workers, int64_t hbm_budget_bytes, qt_server** out);
+/* Runs every queued request, then stops the workers and frees the server. */
+qt_status qt_server_destroy(qt_server* s);
+qt_status qt_server_add_circuit(qt_server* s, qt_circuit* c, int32_t* slot);
+/* Queue a request (edits are copied); *ticket identifies it. */
+qt_status qt_server_submit(qt_server* s, int32_t slot, int32_t nedits, const qt_edit* edits, uint64_t* ticket);
+/* Block until the request is done, copy its result and forget the ticket. */
+qt_status qt_server_wait(qt_server* s, uint64_t ticket, qt_request_result* out);
+/* Device bytes admitted for resident circuits, evictions so far, requests queued. */
+qt_status qt_server_info(qt_server* s, int64_t* resident_bytes, int32_t* evictions, int32_t* queued);
+
 #ifdef __cplusplus
 }
 #endif

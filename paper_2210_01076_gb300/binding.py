@@ -46,7 +46,62 @@ class qt_update_stats(ctypes.Structure):
 EXPORTED = ["qt_create", "qt_destroy", "qt_num_levels", "qt_num_gates", "qt_insert_level", "qt_remove_level",
             "qt_insert_gate", "qt_remove_gate", "qt_replace_gate", "qt_update_state", "qt_read_amplitudes",
             "qt_read_amplitudes_device", "qt_norm", "qt_norm_static", "qt_fidelity", "qt_probabilities",
-            "qt_set_option", "qt_set_stream", "qt_num_segments", "qt_segment_info", "qt_last_error"]
+            "qt_set_option", "qt_set_stream", "qt_num_segments", "qt_segment_info", "qt_last_error",
+            "qt_batch_create", "qt_batch_run", "qt_batch_read_amplitudes", "qt_batch_destroy",
+            "qt_batch_last_error",
+            "qt_release_device", "qt_device_bytes", "qt_server_create", "qt_server_destroy",
+            "qt_server_add_circuit", "qt_server_submit", "qt_server_wait", "qt_server_info"]
+
+QT_EDIT_INSERT_LEVEL, QT_EDIT_INSERT_GATE, QT_EDIT_REMOVE_GATE, QT_EDIT_REPLACE_GATE, QT_EDIT_REMOVE_LEVEL = range(5)
+
+
+class qt_edit(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("level", ctypes.c_int32), ("id", ctypes.c_uint64), ("gate", qt_gate)]
+
+
+class qt_batch_stats(ctypes.Structure):
+    _fields_ = [("gpu_ms", ctypes.c_double), ("circuits", ctypes.c_int32), ("passes", ctypes.c_int32),
+                ("tiles", ctypes.c_int32), ("graph_replayed", ctypes.c_int32), ("amp_updates", ctypes.c_uint64)]
+
+
+class Batch:
+    """Many small circuits re-simulated together in one persistent launch
+    (qt_batch_*); the second and later runs of an unchanged structure replay
+    a CUDA graph."""
+
+    def __init__(self, circuits):
+        self.circuits = list(circuits)
+        arr = (ctypes.c_void_p * len(self.circuits))(*[c.h.value for c in self.circuits])
+        h = ctypes.c_void_p()
+        st = load().qt_batch_create(arr, len(self.circuits), ctypes.byref(h))
+        _check(None, st)
+        self.h = h
+
+    def _check(self, status):
+        if status != QT_OK:
+            raise QtError(status, (load().qt_batch_last_error(self.h) or b"").decode())
+
+    def run(self) -> dict:
+        s = qt_batch_stats()
+        self._check(load().qt_batch_run(self.h, ctypes.byref(s)))
+        return {name: getattr(s, name) for name, _ in qt_batch_stats._fields_}
+
+    def read_amplitudes(self, index: int) -> np.ndarray:
+        c = self.circuits[index]
+        out = np.empty(1 << c.n, np.complex64 if c.dtype == "c64" else np.complex128)
+        self._check(load().qt_batch_read_amplitudes(self.h, index, 0, 1 << c.n, out.ctypes.data))
+        return out
+
+    def close(self):
+        if self.h:
+            load().qt_batch_destroy(self.h)
+            self.h = None
+
+
+class qt_request_result(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("circuit", ctypes.c_int32), ("queue_ms", ctypes.c_double),
+                ("service_ms", ctypes.c_double), ("latency_ms", ctypes.c_double), ("stats", qt_update_stats),
+                ("n_new_ids", ctypes.c_int32), ("reserved", ctypes.c_int32), ("new_ids", ctypes.c_uint64 * 8)]
 
 
 class QtError(RuntimeError):
@@ -90,6 +145,18 @@ def load(path: str = LIB_PATH):
         "qt_set_stream": [P, P],
         "qt_num_segments": [P, ctypes.POINTER(i32)],
         "qt_segment_info": [P, i32, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(i32), P, P],
+        "qt_release_device": [P],
+        "qt_device_bytes": [P, ctypes.POINTER(i64)],
+        "qt_server_create": [i32, i64, ctypes.POINTER(P)],
+        "qt_server_destroy": [P],
+        "qt_server_add_circuit": [P, P, ctypes.POINTER(i32)],
+        "qt_server_submit": [P, i32, i32, ctypes.POINTER(qt_edit), ctypes.POINTER(u64)],
+        "qt_server_wait": [P, u64, ctypes.POINTER(qt_request_result)],
+        "qt_server_info": [P, ctypes.POINTER(i64), ctypes.POINTER(i32), ctypes.POINTER(i32)],
+        "qt_batch_create": [ctypes.POINTER(P), i32, ctypes.POINTER(P)],
+        "qt_batch_run": [P, ctypes.POINTER(qt_batch_stats)],
+        "qt_batch_read_amplitudes": [P, i32, u64, u64, P],
+        "qt_batch_destroy": [P],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -97,6 +164,8 @@ def load(path: str = LIB_PATH):
         f.restype = ctypes.c_int
     lib.qt_last_error.argtypes = [P]
     lib.qt_last_error.restype = ctypes.c_char_p
+    lib.qt_batch_last_error.argtypes = [P]
+    lib.qt_batch_last_error.restype = ctypes.c_char_p
     _lib = lib
     return lib
 
@@ -367,3 +436,78 @@ def apply_edit_ops(circ: Circuit, ops, handle_to_id: dict):
             handle_to_id[nh] = circ.replace_gate(lvl, handle_to_id.pop(h), g)
         else:
             raise ValueError(kind)
+
+
+# ---------------------------------------------------------------- serving
+
+def qt_release_device(h):
+    _check(h, load().qt_release_device(h))
+
+
+def qt_device_bytes(h) -> int:
+    v = ctypes.c_int64()
+    _check(h, load().qt_device_bytes(h, ctypes.byref(v)))
+    return v.value
+
+
+def make_edit(op) -> qt_edit:
+    """('insert_level', level) | ('insert', level, gate) | ('remove', level, id)
+    | ('replace', level, id, gate) | ('remove_level', level)."""
+    e = qt_edit()
+    kind = op[0]
+    e.level = int(op[1])
+    if kind == "insert_level":
+        e.kind = QT_EDIT_INSERT_LEVEL
+    elif kind == "remove_level":
+        e.kind = QT_EDIT_REMOVE_LEVEL
+    elif kind == "insert":
+        e.kind = QT_EDIT_INSERT_GATE
+        e.gate = make_qt_gate(op[2])
+    elif kind == "remove":
+        e.kind = QT_EDIT_REMOVE_GATE
+        e.id = int(op[2])
+    elif kind == "replace":
+        e.kind = QT_EDIT_REPLACE_GATE
+        e.id = int(op[2])
+        e.gate = make_qt_gate(op[3])
+    else:
+        raise ValueError(kind)
+    return e
+
+
+class Server:
+    """Thin wrapper of qt_server_*: requests are lists of edit tuples (see
+    make_edit) followed by an incremental update of one circuit."""
+
+    def __init__(self, workers: int = 8, hbm_budget_bytes: int = 0):
+        h = ctypes.c_void_p()
+        _check(None, load().qt_server_create(workers, hbm_budget_bytes, ctypes.byref(h)))
+        self.h = h
+
+    def add_circuit(self, circ: "Circuit") -> int:
+        slot = ctypes.c_int32()
+        _check(None, load().qt_server_add_circuit(self.h, circ.h, ctypes.byref(slot)))
+        return slot.value
+
+    def submit(self, slot: int, ops) -> int:
+        arr = (qt_edit * max(len(ops), 1))(*[make_edit(o) for o in ops])
+        t = ctypes.c_uint64()
+        _check(None, load().qt_server_submit(self.h, slot, len(ops), arr, ctypes.byref(t)))
+        return t.value
+
+    def wait(self, ticket: int) -> dict:
+        r = qt_request_result()
+        _check(None, load().qt_server_wait(self.h, ticket, ctypes.byref(r)))
+        return {"status": r.status, "circuit": r.circuit, "queue_ms": r.queue_ms, "service_ms": r.service_ms,
+                "latency_ms": r.latency_ms, "stats": stats_dict(r.stats),
+                "new_ids": [r.new_ids[k] for k in range(r.n_new_ids)]}
+
+    def info(self) -> dict:
+        rb, ev, q = ctypes.c_int64(), ctypes.c_int32(), ctypes.c_int32()
+        _check(None, load().qt_server_info(self.h, ctypes.byref(rb), ctypes.byref(ev), ctypes.byref(q)))
+        return {"resident_bytes": rb.value, "evictions": ev.value, "queued": q.value}
+
+    def close(self):
+        if self.h:
+            load().qt_server_destroy(self.h)
+            self.h = None

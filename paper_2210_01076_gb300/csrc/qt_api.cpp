@@ -87,6 +87,7 @@ struct qt_circuit {
     // options
     int ckpt_interval = 4;
     bool fusion = true;
+    bool merge = true;
     int tile_high = 5;  // tiles of 2^11 (complex128) / 2^12 (complex64) amplitudes
     int64_t mem_limit = 0;
     bool kernel_timing = false;
@@ -192,7 +193,32 @@ void free_device(qt_circuit* c) {
     if (c->ev_end) cudaEventDestroy(c->ev_end);
     for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
     c->ev_pool.clear();
-    if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+    if (c->own_stream && c->stream) {
+        cudaStreamDestroy(c->stream);
+        c->stream = nullptr;
+        c->own_stream = false;
+    }
+    // everything is reallocated by the next ensure_device()
+    c->d_ops = nullptr;
+    c->d_ops_cap = 0;
+    c->d_wl = nullptr;
+    c->d_wl_cap = 0;
+    c->h_ops = nullptr;
+    c->h_ops_cap = 0;
+    c->h_wl = nullptr;
+    c->h_wl_cap = 0;
+    c->d_norm_partials = nullptr;
+    c->d_norm_out = nullptr;
+    c->norm_cap = 0;
+    c->d_red = nullptr;
+    c->d_red_cap = 0;
+    c->d_red_out = nullptr;
+    c->d_red_out_cap = 0;
+    c->d_read = nullptr;
+    c->d_read_cap = 0;
+    c->d_err = nullptr;
+    c->h_err = nullptr;
+    c->ev_begin = c->ev_end = nullptr;
     c->device_ready = false;
     c->device_valid = false;
 }
@@ -291,11 +317,13 @@ PlanParams make_params(const qt_circuit* c) {
     pp.lt = std::min(c->p, tile_low_default(c->dtype));
     pp.nh_max = std::max(0, std::min(c->tile_high, c->n - pp.lt));
     pp.fusion = c->fusion;
+    pp.merge = c->merge;
     return pp;
 }
 
 bool same_params(const PlanParams& a, const PlanParams& b) {
-    return a.n == b.n && a.p == b.p && a.lt == b.lt && a.nh_max == b.nh_max && a.fusion == b.fusion;
+    return a.n == b.n && a.p == b.p && a.lt == b.lt && a.nh_max == b.nh_max && a.fusion == b.fusion &&
+           a.merge == b.merge;
 }
 
 DevOp encode_op(int dtype, const Pass& ps, const HostOp& op) {
@@ -657,11 +685,29 @@ qt_status check_readable(qt_circuit* c) {
     qt_status rs = ensure_device(c);
     if (rs != QT_OK) return rs;
     if (c->have_plan && !c->device_valid && !c->plans.empty())
-        return fail(c, QT_ERR_STALE, "the device state is not valid (a previous update failed)");
+        return fail(c, QT_ERR_STALE,
+                    "the state is not on the device (released, or a previous update failed): call qt_update_state");
     return QT_OK;
 }
 
 }  // namespace
+
+// ------------------------------------------------ hooks for batched runs --
+DevOp qt::encode_device_op(int dtype, const Pass& ps, const HostOp& op) { return encode_op(dtype, ps, op); }
+
+void qt::circuit_plan_whole(const qt_circuit* c, std::vector<Pass>* passes, int* dtype, int* n) {
+    PlanParams pp = make_params(c);
+    pp.p = c->n;  // one partition: tiles may use every qubit, no coupling
+    pp.lt = std::min(c->n, tile_low_default(c->dtype));
+    pp.nh_max = std::max(0, std::min(c->tile_high, c->n - pp.lt));
+    std::vector<const qt_gate*> gl;
+    for (const Level& L : c->levels)
+        for (const Gate& g : L.gates) gl.push_back(&g.g);
+    SegPlan sp = plan_segment(gl, pp);
+    *passes = std::move(sp.passes);
+    *dtype = c->dtype;
+    *n = c->n;
+}
 
 // ===================================================================== ABI ==
 #define QT_GUARD_BEGIN try {
@@ -971,6 +1017,8 @@ qt_status qt_set_option(qt_circuit* c, const char* key, int64_t value) {
         c->ckpt_interval = int(value);
     } else if (k == "fusion") {
         c->fusion = value != 0;
+    } else if (k == "merge") {
+        c->merge = value != 0;
     } else if (k == "tile_high") {
         if (value < 0 || value > kMaxTileHigh) return fail(c, QT_ERR_ARG, "tile_high must be in [0, 7]");
         if (tile_low_default(c->dtype) + value > (c->dtype == QT_C64 ? 13 : 12))
@@ -1036,5 +1084,34 @@ qt_status qt_segment_info(const qt_circuit* cc, int32_t seg, int32_t* first_leve
 }
 
 const char* qt_last_error(const qt_circuit* c) { return c ? c->err.c_str() : g_create_error.c_str(); }
+
+qt_status qt_release_device(qt_circuit* c) {
+    if (!c) return QT_ERR_ARG;
+    free_device(c);
+    return QT_OK;
+}
+
+qt_status qt_device_bytes(const qt_circuit* c, int64_t* out) {
+    if (!c || !out) return QT_ERR_ARG;
+    *out = int64_t(qt::circuit_device_bytes(c));
+    return QT_OK;
+}
+
+}  // extern "C"
+
+// -------------------------------------------- hooks for the serving loop --
+size_t qt::circuit_device_bytes(const qt_circuit* c) {
+    return c->device_ready ? c->slabs.size() * c->state_bytes() : 0;
+}
+
+size_t qt::circuit_device_need(const qt_circuit* c) {
+    const size_t L = c->levels.size();
+    const size_t S = (L + size_t(c->ckpt_interval) - 1) / size_t(c->ckpt_interval);
+    return (S + 2) * c->state_bytes();  // checkpoints, and a level's worth of slack for inserted levels
+}
+
+void qt::circuit_release_device(qt_circuit* c) { free_device(c); }
+
+extern "C" {
 
 }  // extern "C"

@@ -19,14 +19,8 @@ struct df {
     float hi, lo;
 };
 
-// Additions written as FMAs whose multiplier is a constant-memory 1.0 the
-// compiler cannot fold: fma(a, 1, b) is the same correctly rounded sum as
-// a + b, but it issues on the FMA pipe, which on this GPU has twice the
-// binary32 rate of the pipe that takes plain additions (ncu pipe counters of
-// the float-float kernels showed the addition pipe saturating first).
-__constant__ float kOneC = 1.0f;
-__device__ __forceinline__ float fadd(float a, float b) { return __fmaf_rn(a, kOneC, b); }
-__device__ __forceinline__ float fsub(float a, float b) { return __fmaf_rn(b, -kOneC, a); }
+__device__ __forceinline__ float fadd(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ float fsub(float a, float b) { return __fsub_rn(a, b); }
 
 __device__ __forceinline__ df two_sum(float a, float b) {
     float s = fadd(a, b);

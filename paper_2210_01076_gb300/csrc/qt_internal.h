@@ -73,6 +73,7 @@ struct PlanParams {
     int lt = 0;        // tile low bits
     int nh_max = 0;    // tile qubits allowed at or above lt
     bool fusion = true;
+    bool merge = true;  // multiply consecutive one-qubit ops on a qubit into one 2x2
 };
 
 // Lower one public gate to primitive ops (A2: gate matrices and classification).
@@ -196,6 +197,38 @@ int launch_norm(int dtype, const void* state, uint64_t namps, double* partials, 
 int norm_partials_needed(uint64_t namps);
 // Message for qt_last_error(NULL) on this thread.
 void set_thread_error(const std::string& msg);
+
+// Serving-loop hooks (qt_api.cpp): device bytes a circuit holds, bytes its
+// next update needs, and releasing its device memory (next update is full).
+size_t circuit_device_bytes(const qt_circuit* c);
+size_t circuit_device_need(const qt_circuit* c);
+void circuit_release_device(qt_circuit* c);
+
+// Batched runs (qt_batch.cpp): the whole circuit planned as one segment with
+// one partition, and the device encoding of an op.
+void circuit_plan_whole(const qt_circuit* c, std::vector<Pass>* passes, int* dtype, int* n);
+DevOp encode_device_op(int dtype, const Pass& ps, const HostOp& op);
+
+// One pass of one circuit in a batched launch.  Work items (tiles) of all
+// passes are numbered in wavefront order: every tile of a circuit's pass i
+// comes after every tile of its pass i-1.
+struct BatchPass {
+    DevPass dp;
+    uint64_t state_off;   // first amplitude of the circuit's state in the batch arena
+    uint32_t first_item;  // global index of the pass's first tile
+    uint32_t ntiles;
+    int32_t dep;          // counter of the circuit's previous pass (-1: none)
+    uint32_t dep_need;    // tiles that counter must reach
+    int32_t counter;      // this pass's counter
+    int32_t pad;
+};
+// Persistent batched launch: every CTA takes tiles in order, waits (bounded,
+// 1 s) until the previous pass of the tile's circuit is complete, runs the
+// tile in place and counts it done.  err is set if a wait expires.
+int launch_batch(int dtype, void* arena, const BatchPass* passes, int npasses, const DevOp* ops,
+                 uint32_t total_items, uint32_t* head, uint32_t* counters, int* err, size_t smem_bytes,
+                 void* stream);
+int launch_batch_init(int dtype, void* arena, uint64_t arena_amps, const uint64_t* firsts, int count, void* stream);
 
 // Reductions (qt_reduce.cu).
 struct QubitList {

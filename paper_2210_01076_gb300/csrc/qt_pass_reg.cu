@@ -22,6 +22,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <type_traits>
 
 #include "qt_arith.cuh"
 #include "qt_internal.h"
@@ -613,6 +614,170 @@ int launch_reg_a(void* dst, const void* src, const DevPass& dp, const DevOp* ops
         case 4: return launch_reg_t<A, 4>(dst, src, dp, ops, worklist, ngroups, err, st);
         case 5: return launch_reg_t<A, 5>(dst, src, dp, ops, worklist, ngroups, err, st);
         default: return int(cudaErrorInvalidConfiguration);
+    }
+}
+
+// ------------------------------------------------------------ batched runs --
+// Many independent circuits in one persistent launch.  Tiles are dequeued
+// from one global counter in wavefront order (all tiles of pass i of every
+// circuit before pass i+1), so every tile a CTA waits for was dequeued
+// earlier by a running CTA whose own dependencies are earlier still: the
+// launch always makes progress, and every wait is bounded anyway.
+__device__ __forceinline__ uint32_t ld_acquire(const uint32_t* p) {
+    uint32_t v;
+    asm volatile("ld.acquire.gpu.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ bool wait_counter(const uint32_t* c, uint32_t need) {
+    if (ld_acquire(c) >= need) return true;
+    const uint64_t t0 = global_ns();
+    while (ld_acquire(c) < need) {
+        if (global_ns() - t0 > 1000000000ull) return false;
+        __nanosleep(100);
+    }
+    return true;
+}
+
+template <class A, int RB>
+__device__ __forceinline__ void batch_tile(typename A::amp_t* __restrict__ state, const DevPass& dp, uint32_t t,
+                                           const DevOp* __restrict__ ops, typename A::amp_t* tile,
+                                           uint64_t* choff) {
+    using cx = typename A::cx;
+    constexpr int R = 1 << RB;
+    const uint32_t lane = threadIdx.x & 31u, wid = threadIdx.x >> 5;
+    const uint64_t base = tile_base(dp, nullptr, t);
+    chunk_offsets(dp, choff);
+    uint32_t rpos, jw;
+    init_layout<RB>(dp, lane, wid, rpos, jw);
+    __syncthreads();
+    const uint32_t lowmask = (1u << dp.lt) - 1u;
+    cx x[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const uint32_t j = jw | joff<RB>(rpos, r);
+        x[r] = A::ld(__ldcg(&state[base | choff[j >> dp.lt] | (j & lowmask)]));  // L2: written by other SMs
+    }
+    run_ops<A, RB>(x, ops + dp.op_offset, dp.nops, base, lane, wid, rpos, jw, tile);
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const uint32_t j = jw | joff<RB>(rpos, r);
+        state[base | choff[j >> dp.lt] | (j & lowmask)] = A::st(x[r]);
+    }
+    __threadfence();  // every thread's stores are visible device-wide before the tile is counted done
+    __syncthreads();  // choff and tile are reused by the next item
+}
+
+template <class A>
+__global__ void __launch_bounds__(256) k_batch(typename A::amp_t* __restrict__ arena,
+                                               const BatchPass* __restrict__ passes, int npasses,
+                                               const DevOp* __restrict__ ops, uint32_t total_items,
+                                               uint32_t* __restrict__ head, uint32_t* __restrict__ counters,
+                                               int* __restrict__ err) {
+    using amp_t = typename A::amp_t;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    amp_t* tile = reinterpret_cast<amp_t*>(smem_raw);
+    __shared__ uint64_t choff[1 << kMaxTileHigh];
+    __shared__ uint32_t s_item;
+    for (;;) {
+        if (threadIdx.x == 0) s_item = atomicAdd(head, 1u);
+        __syncthreads();
+        const uint32_t item = s_item;
+        __syncthreads();
+        if (item >= total_items) return;
+        int lo = 0, hi = npasses - 1;  // last pass whose first item <= item
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (passes[mid].first_item <= item) lo = mid;
+            else hi = mid - 1;
+        }
+        const BatchPass* bp = passes + lo;
+        bool ok = true;
+        if (threadIdx.x == 0 && bp->dep >= 0) ok = wait_counter(counters + bp->dep, bp->dep_need);
+        if (__syncthreads_or(!ok)) {
+            if (threadIdx.x == 0) atomicExch(err, 1);
+            return;
+        }
+        __threadfence();
+        const DevPass dp = bp->dp;
+        amp_t* state = arena + bp->state_off;
+        const uint32_t t = item - bp->first_item;
+        switch (dp.nreg) {
+            case 2: batch_tile<A, 2>(state, dp, t, ops, tile, choff); break;
+            case 3: batch_tile<A, 3>(state, dp, t, ops, tile, choff); break;
+            case 4: batch_tile<A, 4>(state, dp, t, ops, tile, choff); break;
+            default: break;
+        }
+        if (threadIdx.x == 0) {
+            __threadfence();
+            atomicAdd(counters + bp->counter, 1u);
+        }
+    }
+}
+
+template <class A>
+__global__ void k_batch_init(typename A::amp_t* arena, const uint64_t* __restrict__ firsts, int count) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < count) {
+        typename A::cx one;
+        if constexpr (sizeof(typename A::amp_t) == 8) one = A::ld(make_float2(1.0f, 0.0f));
+        else if constexpr (std::is_same<A, ArDF>::value) one = A::ld(make_float4(1.0f, 0.0f, 0.0f, 0.0f));
+        else one = A::ld(make_double2(1.0, 0.0));
+        arena[firsts[i]] = A::st(one);
+    }
+}
+
+int launch_batch_init(int dtype, void* arena, uint64_t arena_amps, const uint64_t* firsts, int count, void* stream) {
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const size_t bpa = bytes_per_amp(dtype);
+    cudaError_t e = cudaMemsetAsync(arena, 0, arena_amps * bpa, st);
+    if (e != cudaSuccess) return int(e);
+    const int grid = (count + 255) / 256;
+    if (grid == 0) return 0;
+    switch (dtype) {
+        case QT_C128: k_batch_init<ArF64><<<grid, 256, 0, st>>>(static_cast<double2*>(arena), firsts, count); break;
+        case QT_C64: k_batch_init<ArF32><<<grid, 256, 0, st>>>(static_cast<float2*>(arena), firsts, count); break;
+        default: k_batch_init<ArDF><<<grid, 256, 0, st>>>(static_cast<float4*>(arena), firsts, count); break;
+    }
+    return int(cudaGetLastError());
+}
+
+template <class A>
+int launch_batch_t(void* arena, const BatchPass* passes, int npasses, const DevOp* ops, uint32_t total_items,
+                   uint32_t* head, uint32_t* counters, int* err, size_t smem, cudaStream_t st) {
+    static bool attr_set = false;
+    static int nsm = 0;
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(k_batch<A>, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
+        if (e != cudaSuccess) return int(e);
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+        attr_set = true;
+    }
+    if (smem > 64 * 1024) return int(cudaErrorInvalidConfiguration);
+    int per_sm = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch<A>, 256, smem);
+    if (e != cudaSuccess) return int(e);
+    if (per_sm < 1) per_sm = 1;
+    const uint64_t grid = std::min<uint64_t>(total_items, uint64_t(nsm) * uint64_t(per_sm));
+    if (grid == 0) return 0;
+    k_batch<A><<<unsigned(grid), 256, smem, st>>>(static_cast<typename A::amp_t*>(arena), passes, npasses, ops,
+                                                  total_items, head, counters, err);
+    return int(cudaGetLastError());
+}
+
+int launch_batch(int dtype, void* arena, const BatchPass* passes, int npasses, const DevOp* ops,
+                 uint32_t total_items, uint32_t* head, uint32_t* counters, int* err, size_t smem_bytes,
+                 void* stream) {
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    switch (dtype) {
+        case QT_C128: return launch_batch_t<ArF64>(arena, passes, npasses, ops, total_items, head, counters, err,
+                                                   smem_bytes, st);
+        case QT_C64: return launch_batch_t<ArF32>(arena, passes, npasses, ops, total_items, head, counters, err,
+                                                  smem_bytes, st);
+        default: return launch_batch_t<ArDF>(arena, passes, npasses, ops, total_items, head, counters, err,
+                                             smem_bytes, st);
     }
 }
 

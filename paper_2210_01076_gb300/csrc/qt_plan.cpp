@@ -326,7 +326,7 @@ SegPlan plan_segment(const std::vector<const qt_gate*>& gates, const PlanParams&
         std::vector<int> last(pp.n, -1);  // index into merged of the last op touching q
         for (const HostOp& op : ops) {
             uint64_t qs = op_qubits(op);
-            if (single_qubit(op) && last[op.q0] >= 0 && single_qubit(merged[last[op.q0]]) &&
+            if (pp.merge && single_qubit(op) && last[op.q0] >= 0 && single_qubit(merged[last[op.q0]]) &&
                 merged[last[op.q0]].q0 == op.q0) {
                 HostOp& prev = merged[last[op.q0]];
                 M2 a, b;
@@ -351,6 +351,12 @@ SegPlan plan_segment(const std::vector<const qt_gate*>& gates, const PlanParams&
             if (!ident) ps.ops.push_back(op);
         }
         ps.lt = pp.lt;
+        // Pad the tile to its full size with qubits inside the partition
+        // (they add no coupling between partitions): larger tiles amortise
+        // the per-op work over more amplitudes per thread and keep every
+        // pass on the register kernel.
+        for (int q = pp.lt; q < std::min(pp.p, pp.n) && popcount64(H) < pp.nh_max; ++q)
+            H |= uint64_t(1) << q;
         ps.nh = 0;
         for (int q = pp.lt; q < pp.n; ++q)
             if ((H >> q) & 1) ps.h[ps.nh++] = q;

@@ -1,0 +1,82 @@
+"""Batched runs (qt_batch_*): many small circuits of uneven qubit counts in
+one persistent launch, then CUDA-graph replays after parameter edits."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2210_01076_gb300 import binding as B
+from paper_2210_01076_gb300 import build as qbuild
+from paper_2210_01076_gb300 import workloads as W
+from gpu_helpers import TOL, max_err
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    qbuild.build()
+    B.load()
+
+
+def rotation_handles(levels, ids):
+    return [(l, k) for l, lv in enumerate(levels) for k, g in enumerate(lv) if g.name in ("rz", "ry")]
+
+
+@pytest.mark.parametrize("dtype", ["c128df", "c64", "c128"])
+def test_batch_matches_oracle_and_replays_after_parameter_edits(dtype):
+    rng = np.random.default_rng(7)
+    circs, levels, ids = [], [], []
+    for k in range(9):
+        n = int(rng.integers(10, 15))
+        lv = W.random_circuit(n, int(rng.integers(40, 160)), seed=300 + k, p_multi=0.4)
+        c = B.Circuit(n, dtype, min(n, 10))
+        ids.append(c.load_levels(lv))
+        levels.append([list(x) for x in lv])
+        circs.append(c)
+    batch = B.Batch(circs)
+    for rnd in range(4):
+        st = batch.run()
+        assert st["circuits"] == 9 and st["tiles"] > 0
+        if rnd >= 2:
+            assert st["graph_replayed"] == 1
+        for k, c in enumerate(circs):
+            want = oracle.simulate(c.n, W.flatten(levels[k]))
+            assert max_err(batch.read_amplitudes(k), want) <= TOL[dtype], (rnd, k)
+        # a parameter edit per circuit: a rotation angle moves by N(0, 0.1)
+        for k, c in enumerate(circs):
+            cand = rotation_handles(levels[k], ids[k])
+            if not cand:
+                continue
+            l, j = cand[int(rng.integers(len(cand)))]
+            g = levels[k][l][j]
+            ng = g._replace(params=(g.params[0] + float(rng.normal(0.0, 0.1)),))
+            ids[k][l][j] = c.replace_gate(l, ids[k][l][j], ng)
+            levels[k][l][j] = ng
+    # a structural edit: a new gate and level in one circuit -> a new graph
+    circs[0].insert_level(0)
+    g = W.make_gate("h", [0])
+    circs[0].insert_gate(0, g)
+    levels[0].insert(0, [g])
+    st = batch.run()
+    assert st["graph_replayed"] == 0
+    assert max_err(batch.read_amplitudes(0), oracle.simulate(circs[0].n, W.flatten(levels[0]))) <= TOL[dtype]
+    batch.close()
+
+
+def test_batch_rejects_mixed_dtypes_and_tiny_circuits():
+    a = B.Circuit(10, "c64", 10)
+    b = B.Circuit(10, "c128df", 10)
+    a.load_levels([[W.make_gate("h", [0])]])
+    b.load_levels([[W.make_gate("h", [0])]])
+    batch = B.Batch([a, b])
+    with pytest.raises(B.QtError):
+        batch.run()
+    batch.close()
+    t = B.Circuit(6, "c64", 6)
+    t.load_levels([[W.make_gate("h", [0])]])
+    batch = B.Batch([t])
+    with pytest.raises(B.QtError):
+        batch.run()
+    batch.close()
