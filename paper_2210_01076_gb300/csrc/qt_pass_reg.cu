@@ -326,8 +326,23 @@ __device__ __forceinline__ void run_ops(typename A::cx (&x)[1 << RB], const DevO
                                         typename A::amp_t* tile) {
     using RO = RegOps<A, RB>;
     constexpr int R = 1 << RB;
-    for (int oi = 0; oi < nops; ++oi) {
-        const DevOp* op = pops + oi;
+    // The ops are staged in shared memory, a chunk at a time: every thread
+    // reads every field of every op, and a shared-memory broadcast keeps
+    // that off the critical path that a global load per field would be on.
+    constexpr int kOpChunk = 64;
+    __shared__ __align__(16) DevOp s_ops[kOpChunk];
+    for (int c0 = 0; c0 < nops; c0 += kOpChunk) {
+    const int cn = nops - c0 < kOpChunk ? nops - c0 : kOpChunk;
+    __syncthreads();  // the previous chunk has been read by all
+    {
+        const uint4* srcv = reinterpret_cast<const uint4*>(pops + c0);
+        uint4* dstv = reinterpret_cast<uint4*>(s_ops);
+        constexpr int kVec = int(sizeof(DevOp) / sizeof(uint4));
+        for (int i = threadIdx.x; i < cn * kVec; i += blockDim.x) dstv[i] = srcv[i];
+    }
+    __syncthreads();
+    for (int oi = 0; oi < cn; ++oi) {
+        const DevOp* op = s_ops + oi;
         const int kind = op->kind;
         if (kind == OP_PERM) {
             __syncthreads();  // the previous layout change has been read by all
@@ -407,6 +422,7 @@ __device__ __forceinline__ void run_ops(typename A::cx (&x)[1 << RB], const DevO
             default:
                 break;
         }
+    }
     }
 }
 
@@ -705,7 +721,9 @@ __global__ void __launch_bounds__(256) k_batch(typename A::amp_t* __restrict__ a
         switch (dp.nreg) {
             case 2: batch_tile<A, 2>(state, dp, t, ops, tile, choff); break;
             case 3: batch_tile<A, 3>(state, dp, t, ops, tile, choff); break;
-            case 4: batch_tile<A, 4>(state, dp, t, ops, tile, choff); break;
+            case 4:  // tiles of 2^12 occur for complex64 only (16-byte amplitudes stop at 2^11)
+                if constexpr (sizeof(amp_t) == 8) batch_tile<A, 4>(state, dp, t, ops, tile, choff);
+                break;
             default: break;
         }
         if (threadIdx.x == 0) {
