@@ -80,3 +80,24 @@ def test_batch_rejects_mixed_dtypes_and_tiny_circuits():
     with pytest.raises(B.QtError):
         batch.run()
     batch.close()
+
+
+def test_autotuners_pick_a_measured_setting():
+    from paper_2210_01076_gb300 import tuning
+    n = 14
+    levels = W.random_circuit(n, 200, seed=12, p_multi=0.4)
+    res = tuning.tune_circuit(n, "c128df", levels, 8, tile_high=(3, 5), merge=(0, 1), repeats=1)
+    assert res["best"] is not None and len(res["table"]) == 4
+    c = B.Circuit(n, "c128df", 8)
+    for k, v in res["best"]["options"].items():
+        c.set_option(k, v)
+    c.load_levels(levels)
+    c.update_state()
+    assert max_err(c.read_amplitudes(), oracle.simulate(n, W.flatten(levels))) <= 1e-12
+    circs = []
+    for k in range(4):
+        cc = B.Circuit(11 + k, "c64", 11 + k)
+        cc.load_levels(W.random_circuit(11 + k, 80, seed=k))
+        circs.append(cc)
+    bt = tuning.tune_batch(circs, tile_high=(3, 5), repeats=1)
+    assert bt["best"] is not None and len(bt["table"]) == 2
