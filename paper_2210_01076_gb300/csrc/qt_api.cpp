@@ -369,9 +369,9 @@ DevOp encode_op(int dtype, const Pass& ps, const HostOp& op) {
         default: break;
     }
     // tile-local control mask (the register-layout planner splits it)
-    d.cm_thr = 0;
+    d.cm_tile = 0;
     for (int q = 0; q < 64; ++q)
-        if (((op.cmask & tile_mask) >> q) & 1) d.cm_thr |= 1u << loc(q);
+        if (((op.cmask & tile_mask) >> q) & 1) d.cm_tile |= 1u << loc(q);
     std::sort(fixed.begin(), fixed.end());
     d.nfix = uint8_t(fixed.size());
     d.fixval = 0;
@@ -550,7 +550,7 @@ qt_status do_update(qt_circuit* c, int force_full, qt_update_stats* stats) {
             std::vector<DevOp> pops;
             pops.reserve(ps.ops.size());
             for (const HostOp& o : ps.ops) pops.push_back(encode_op(c->dtype, ps, o));
-            if (c->reg_kernel) plan_register_layout(&dp, &pops);
+            if (c->reg_kernel) plan_register_layout(&dp, &pops, int(bytes_per_amp(c->dtype)));
             dp.tma = (dp.reg_kernel && c->tma) ? 1 : 0;
             dp.test_stall = c->test_stall ? 1 : 0;
             dp.nops = int32_t(pops.size());

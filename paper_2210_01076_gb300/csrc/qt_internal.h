@@ -2,6 +2,7 @@
 // of libqtask.so.  Not part of the public ABI (include/qtask.h is).
 #pragma once
 
+#include <cstddef>
 #include <cstdint>
 #include <string>
 #include <vector>
@@ -116,9 +117,9 @@ void close_forward(Bitset* D, const Pass& ps, const Bitset& supp);
 void close_all(Bitset* W, const std::vector<Pass>& passes, const std::vector<Bitset>& supps);
 
 // ------------------------------------------------------- device encoding --
-// One op as the kernels read it (96 bytes).  Matrix entries are stored in the
-// arithmetic of the circuit's dtype: binary64 (QT_C128), binary32 (QT_C64) or
-// float-float (hi, lo) pairs (QT_C128_DF).
+// One op as the kernels read it (128 bytes).  Matrix entries are stored in
+// the arithmetic of the circuit's dtype: binary64 (QT_C128), binary32
+// (QT_C64) or float-float (hi, lo) pairs (QT_C128_DF).
 //
 // Two kernels read it.  The shared-memory kernel (small tiles) walks the
 // op's index pattern (fixpos/fixval).  The register kernel (tiles of 2^7 and
@@ -126,14 +127,62 @@ void close_all(Bitset* W, const std::vector<Pass>& passes, const std::vector<Bit
 // lane bits, the other tile bits are split between register-index bits and
 // warp bits by the current layout; OP_PERM ops change the layout through
 // shared memory so that every target is a lane or register bit when its op
-// runs.  Roles: 0..7 = register-index bit, kRoleLane + b = lane bit b,
-// kRoleThread + t = tile bit t held by the lane or warp index (DIAG only),
-// kRoleNone = outside the tile.
-constexpr int8_t kRoleLane = 32;
-constexpr int8_t kRoleThread = 64;
-constexpr int8_t kRoleNone = -1;
-
+// runs.  The layout planner resolves every op against the layout it runs in
+// and writes the result to DevOp::rh.
 enum : int32_t { OP_PERM = 7 };  // register-kernel layout change
+
+// Where a tile's bits sit in the register kernel: the tile bit held by each
+// lane-id bit, register-index bit and warp-id bit, and the pending flip.  A
+// thread's amplitude at physical slot P (its lane, register index and warp)
+// is the tile's amplitude at index L(P) ^ flip: uncontrolled X gates only
+// toggle flip and uncontrolled SWAP gates only exchange two entries, so
+// neither moves data; the next layout change or the final store applies
+// both.
+struct TileLayout {
+    int8_t lane[5];
+    int8_t reg[5];
+    int8_t warp[3];
+    int8_t pad[3];
+    uint32_t flip;
+};
+static_assert(sizeof(TileLayout) == 20, "TileLayout layout");
+
+// Register-kernel dispatch code of an op: its kind and where its qubits sit
+// in the thread's layout (register bit 0 after the rename, a lane bit, a bit
+// held by the thread or outside the tile), chosen on the host so that the
+// kernel takes one branch per op.
+enum RegCode : uint8_t {
+    RC_PERM = 0,
+    RC_DENSE_R, RC_DENSE_L,  // _R: target on register bit 0, _L: on lane bit a
+    RC_REAL_R, RC_REAL_L,
+    RC_ANTI_R, RC_ANTI_L,
+    RC_X_R, RC_X_L,
+    RC_SWAP_RR,  // register bits a < b
+    RC_SWAP_LR,  // lane bit a, register bit b
+    RC_SWAP_LL,  // lane bits a, b
+    RC_DIAG_G,   // qubit a outside the tile: one factor per tile
+    RC_DIAG_T,   // thread-index bit a (lane bits 0-4, warp bits 5-7): one factor per thread
+    RC_DIAG_R,   // register bit a
+    RC_PH_NEG, RC_PH_POS_I, RC_PH_NEG_I, RC_PH_GEN,
+    RC_NOP
+};
+
+// Everything the register kernel reads per op besides cm_glob and the
+// matrix, in one 16-byte load.  Conditions are on physical bits: the thread
+// index (lane bits 0-4, warp bits 5-7) and the register index; an op applies
+// where (bits ^ value) & mask == mask, the value marking conditions on
+// flipped tile bits.
+struct RegHdr {
+    uint8_t code;     // RegCode
+    int8_t ren;       // > 0: exchange register bits 0 and ren before the op (pair ops)
+    int8_t a, b;      // code-specific bits (see RegCode)
+    uint16_t cm_reg;  // conditions among register-index bits
+    uint8_t mcls;     // PHASE: 0 no register condition, 1 exactly one unflipped (bit in a), 2 otherwise
+    uint8_t cv_reg;   // flipped register conditions
+    uint32_t cm_thr;  // conditions among thread-index bits
+    uint32_t cv_thr;  // flipped thread conditions
+};
+static_assert(sizeof(RegHdr) == 16, "RegHdr layout");
 
 struct DevOp {
     int32_t kind;
@@ -144,19 +193,19 @@ struct DevOp {
     int8_t fixpos[6];  // tile-local bits fixed by the op's index pattern, ascending
     uint8_t nfix;      // number of fixed bits; the op visits 2^(tile bits - nfix) indices
     uint8_t fixval;    // bit k = value of fixpos[k]
-    uint32_t cm_thr;   // register kernel: control bits among lane and warp tile bits
-    uint16_t cm_reg;   // register kernel: control bits among register-index bits
-    int8_t role0, role1;  // register kernel: roles of q0 and q1
+    uint32_t cm_tile;  // control bits inside the tile (tile-local positions)
     int8_t sub;        // PhaseKind (PHASE)
     int8_t nreg, nwarp;  // OP_PERM: register bits and warp bits of the new layout
-    int8_t perm[8];    // OP_PERM: tile bit of register bit k (k < nreg), then of warp bit w
-    int8_t pad[9];
+    int8_t pad0;
+    int8_t perm[8];    // OP_PERM: tile bit of register bit k (k < nreg), then of warp bit w, in the
+                       // new layout (lane bit i holds tile bit i); m holds the old TileLayout
+    RegHdr rh;         // register kernel (filled by the layout planner)
     union {
         double d[8];
         float f[16];
     } m;
 };
-static_assert(sizeof(DevOp) == 128, "DevOp layout");
+static_assert(sizeof(DevOp) == 128 && offsetof(DevOp, rh) == 48 && offsetof(DevOp, m) == 64, "DevOp layout");
 
 struct DevPass {
     int32_t p;             // log2 partition size
@@ -175,11 +224,15 @@ struct DevPass {
     int32_t layout[8];     // tile bit of register bit k (k < nreg), then of warp bit w
     int32_t tma;           // 1: persistent register kernel with bulk-copy (TMA) staging
     int32_t test_stall;    // 1: withhold the staging copies so the bounded wait expires (test hook)
+    TileLayout fin;        // register kernel: the layout the tile is stored from
 };
 
 // Register-kernel layout planning for one pass (host): fills the initial
 // layout of dp and rewrites the ops' roles, inserting OP_PERM where needed.
-void plan_register_layout(DevPass* dp, std::vector<DevOp>* ops);
+// coef_bytes: size of one complex matrix entry (16 for binary64 and
+// float-float, 8 for binary32), for exchanging entries when an op's target
+// is flipped.
+void plan_register_layout(DevPass* dp, std::vector<DevOp>* ops, int coef_bytes);
 
 // Kernel launchers (qt_kernels.cu).  Return a cudaError_t as int.
 // err: device int set to 1 when a bounded wait of the TMA-staged kernel

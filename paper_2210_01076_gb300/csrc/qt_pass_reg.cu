@@ -54,9 +54,6 @@ __device__ __forceinline__ void dispatch_k(int k, F&& f) {
     }
 }
 
-// Register layout: tile bit of register-index bit k, packed 5 bits per k.
-__device__ __forceinline__ uint32_t field5(uint32_t packed, int k) { return (packed >> (5 * k)) & 31u; }
-
 template <class A, int RB>
 struct RegOps {
     using cx = typename A::cx;
@@ -76,12 +73,12 @@ struct RegOps {
         }
     }
 
-    // one-target ops on register bit 0: pairs (x[2i], x[2i+1]).  DENSE, REAL,
-    // ANTI and DIAG ops never carry controls (only X, SWAP and PHASE do; the
+    // one-target ops on register bit 0: pairs (x[2i], x[2i+1]).  DENSE, REAL
+    // and ANTI ops never carry conditions (only X, SWAP and PHASE do; the
     // host checks it), so their loops need no per-amplitude predicate.
-    static __device__ __forceinline__ void pair_reg0(int kind, cx (&x)[R], const DevOp* op, bool thr_ok,
-                                                     uint32_t cmr) {
-        if (kind == OP_DENSE) {
+    template <int KIND>
+    static __device__ __forceinline__ void pair_reg0(cx (&x)[R], const DevOp* op) {
+        if constexpr (KIND == OP_DENSE) {
             const cx u00 = A::matp(op, 0), u01 = A::matp(op, 1), u10 = A::matp(op, 2), u11 = A::matp(op, 3);
 #pragma unroll
             for (int r = 0; r < R; r += 2) {
@@ -89,21 +86,13 @@ struct RegOps {
                 x[r] = A::lin2(u00, a, u01, b);
                 x[r + 1] = A::lin2(u10, a, u11, b);
             }
-        } else if (kind == OP_REAL) {
+        } else if constexpr (KIND == OP_REAL) {
             const cx u00 = A::matp(op, 0), u01 = A::matp(op, 1), u10 = A::matp(op, 2), u11 = A::matp(op, 3);
 #pragma unroll
             for (int r = 0; r < R; r += 2) {
                 const cx a = x[r], b = x[r + 1];
                 x[r] = A::lin2r(u00, a, u01, b);
                 x[r + 1] = A::lin2r(u10, a, u11, b);
-            }
-        } else if (kind == OP_X) {
-#pragma unroll
-            for (int r = 0; r < R; r += 2) {
-                if (!(thr_ok && (uint32_t(r) & cmr) == cmr)) continue;
-                const cx a = x[r];
-                x[r] = x[r + 1];
-                x[r + 1] = a;
             }
         } else {  // OP_ANTI
             const cx m01 = A::matp(op, 0), m10 = A::matp(op, 1);
@@ -116,53 +105,56 @@ struct RegOps {
         }
     }
 
+    static __device__ __forceinline__ void x_reg0(cx (&x)[R], bool thr_ok, uint32_t cmr, uint32_t cvr) {
+#pragma unroll
+        for (int r = 0; r < R; r += 2) {
+            if (!(thr_ok && ((uint32_t(r) ^ cvr) & cmr) == cmr)) continue;
+            const cx a = x[r];
+            x[r] = x[r + 1];
+            x[r + 1] = a;
+        }
+    }
+
     // one-target ops on lane bit b: the partner amplitude p comes from lane ^
     // 2^b.  A lane whose bit is 0 computes u00 x + u01 p, a lane whose bit is
     // 1 computes u11 x + u10 p: the coefficients are chosen once per op.
-    static __device__ __forceinline__ void pair_lane(int kind, cx (&x)[R], const DevOp* op, int b, uint32_t lane,
-                                                     bool thr_ok, uint32_t cmr) {
+    template <int KIND>
+    static __device__ __forceinline__ void pair_lane(cx (&x)[R], const DevOp* op, int b, uint32_t lane) {
         const int mask = 1 << b;
-        const bool hi = (lane >> b) & 1u;
-        if (kind == OP_DENSE || kind == OP_REAL) {
-            const cx cs = A::sel(hi, A::matp(op, 3), A::matp(op, 0));  // coefficient of the own amplitude
-            const cx cp = A::sel(hi, A::matp(op, 2), A::matp(op, 1));  // coefficient of the partner's
-            if (kind == OP_DENSE) {
-#pragma unroll
-                for (int r = 0; r < R; ++r) {
-                    const cx p = A::shfl(x[r], mask);
-                    x[r] = A::lin2(cs, x[r], cp, p);
-                }
-            } else {
-#pragma unroll
-                for (int r = 0; r < R; ++r) {
-                    const cx p = A::shfl(x[r], mask);
-                    x[r] = A::lin2r(cs, x[r], cp, p);
-                }
-            }
-        } else if (kind == OP_X) {
+        const int hi = int((lane >> b) & 1u);
+        if constexpr (KIND == OP_DENSE || KIND == OP_REAL) {
+            const cx cs = A::sel(hi, A::matp(op, 3), A::matp(op, 0));
+            const cx cp = A::sel(hi, A::matp(op, 2), A::matp(op, 1));
 #pragma unroll
             for (int r = 0; r < R; ++r) {
                 const cx p = A::shfl(x[r], mask);
-                if (thr_ok && (uint32_t(r) & cmr) == cmr) x[r] = p;
+                if constexpr (KIND == OP_DENSE) x[r] = A::lin2(cs, x[r], cp, p);
+                else x[r] = A::lin2r(cs, x[r], cp, p);
             }
         } else {  // OP_ANTI: bit-0 output m01 a1, bit-1 output m10 a0
             const cx c = A::sel(hi, A::matp(op, 1), A::matp(op, 0));
 #pragma unroll
-            for (int r = 0; r < R; ++r) {
-                const cx p = A::shfl(x[r], mask);
-                x[r] = A::mul(c, p);
-            }
+            for (int r = 0; r < R; ++r) x[r] = A::mul(c, A::shfl(x[r], mask));
+        }
+    }
+
+    static __device__ __forceinline__ void x_lane(cx (&x)[R], int b, bool thr_ok, uint32_t cmr, uint32_t cvr) {
+        const int mask = 1 << b;
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const cx p = A::shfl(x[r], mask);
+            if (thr_ok && ((uint32_t(r) ^ cvr) & cmr) == cmr) x[r] = p;
         }
     }
 
     // SWAP on register bits K0 < K1: exchange (bit K0, bit K1) = (1,0) and (0,1)
     template <int K0, int K1>
-    static __device__ __forceinline__ void swap_rr(cx (&x)[R], bool thr_ok, uint32_t cmr) {
+    static __device__ __forceinline__ void swap_rr(cx (&x)[R], bool thr_ok, uint32_t cmr, uint32_t cvr) {
 #pragma unroll
         for (int r = 0; r < R; ++r) {
             if (!((r >> K0) & 1) || ((r >> K1) & 1)) continue;
             const int r2 = r ^ ((1 << K0) | (1 << K1));
-            if (!(thr_ok && (uint32_t(r) & cmr) == cmr)) continue;
+            if (!(thr_ok && ((uint32_t(r) ^ cvr) & cmr) == cmr)) continue;
             const cx a = x[r];
             x[r] = x[r2];
             x[r2] = a;
@@ -171,7 +163,8 @@ struct RegOps {
 
     // SWAP of lane bit b with register bit K
     template <int K>
-    static __device__ __forceinline__ void swap_lr(cx (&x)[R], int b, uint32_t lane, bool thr_ok, uint32_t cmr) {
+    static __device__ __forceinline__ void swap_lr(cx (&x)[R], int b, uint32_t lane, bool thr_ok, uint32_t cmr,
+                                                   uint32_t cvr) {
         const int mask = 1 << b;
         const bool lb = (lane >> b) & 1u;
 #pragma unroll
@@ -182,7 +175,7 @@ struct RegOps {
             // partner of (1,0) is (0,1) at lane ^ b, register r1, and back
             const cx from_r1 = A::shfl(x[r1], mask);
             const cx from_r = A::shfl(x[r], mask);
-            if (!(thr_ok && (uint32_t(r) & cmr) == cmr)) continue;
+            if (!(thr_ok && ((uint32_t(r) ^ cvr) & cmr) == cmr)) continue;
             if (lb) x[r] = from_r1;
             else x[r1] = from_r;
         }
@@ -190,40 +183,39 @@ struct RegOps {
 
     // SWAP of two lane bits
     static __device__ __forceinline__ void swap_ll(cx (&x)[R], int b0, int b1, uint32_t lane, bool thr_ok,
-                                                   uint32_t cmr) {
+                                                   uint32_t cmr, uint32_t cvr) {
         const int mask = (1 << b0) | (1 << b1);
         const bool differ = ((lane >> b0) ^ (lane >> b1)) & 1u;
 #pragma unroll
         for (int r = 0; r < R; ++r) {
             const cx p = A::shfl(x[r], mask);
-            if (differ && thr_ok && (uint32_t(r) & cmr) == cmr) x[r] = p;
+            if (differ && thr_ok && ((uint32_t(r) ^ cvr) & cmr) == cmr) x[r] = p;
         }
     }
 
-    // diag(d0, d1) on a qubit whose value for x[r] is bit k of r (k >= 0) or
-    // the per-thread bit tb (k < 0)
-    static __device__ __forceinline__ void diag(cx (&x)[R], const DevOp* op, int k, bool tbit) {
-        const cx d0 = A::matp(op, 0), d1 = A::matp(op, 1);
-        if (k < 0) {
-            const cx d = A::sel(tbit, d1, d0);
+    // diag(d0, d1) on a qubit whose value is the same for all of the
+    // thread's amplitudes (tbit), or is bit k of the register index
+    static __device__ __forceinline__ void diag_u(cx (&x)[R], const DevOp* op, int tbit) {
+        const cx d = A::sel(tbit, A::matp(op, 1), A::matp(op, 0));
 #pragma unroll
-            for (int r = 0; r < R; ++r) x[r] = A::mul(d, x[r]);
-        } else {
-#pragma unroll
-            for (int r = 0; r < R; ++r) x[r] = A::mul(A::sel((r >> k) & 1, d1, d0), x[r]);
-        }
+        for (int r = 0; r < R; ++r) x[r] = A::mul(d, x[r]);
     }
 
-    // multiply the amplitudes whose condition bits are all 1 by the phase;
-    // registers that cannot qualify are skipped at compile time when the
-    // condition has at most one register bit
+    static __device__ __forceinline__ void diag_r(cx (&x)[R], const DevOp* op, int k) {
+#pragma unroll
+        for (int r = 0; r < R; ++r) x[r] = A::mul(A::matp(op, (r >> k) & 1), x[r]);
+    }
+
+    // multiply the amplitudes whose conditions hold by the phase; with one
+    // unflipped register condition bit (mcls 1, bit k) the registers that
+    // cannot qualify are skipped at compile time
     template <class F>
-    static __device__ __forceinline__ void masked(cx (&x)[R], uint32_t cmr, F&& f) {
-        if (cmr == 0) {
+    static __device__ __forceinline__ void masked(cx (&x)[R], int mcls, int k, uint32_t cmr, uint32_t cvr, F&& f) {
+        if (mcls == 0) {
 #pragma unroll
             for (int r = 0; r < R; ++r) x[r] = f(x[r]);
-        } else if ((cmr & (cmr - 1)) == 0) {
-            dispatch_k<RB>(__ffs(cmr) - 1, [&](auto kc) {
+        } else if (mcls == 1) {
+            dispatch_k<RB>(k, [&](auto kc) {
                 constexpr int K = decltype(kc)::value;
 #pragma unroll
                 for (int r = 0; r < R; ++r)
@@ -232,22 +224,7 @@ struct RegOps {
         } else {
 #pragma unroll
             for (int r = 0; r < R; ++r)
-                if ((uint32_t(r) & cmr) == cmr) x[r] = f(x[r]);
-        }
-    }
-
-    static __device__ __forceinline__ void phase(cx (&x)[R], const DevOp* op, bool thr_ok, uint32_t cmr) {
-        if (!thr_ok) return;  // a condition bit held by the lane or warp index is 0
-        const int sub = op->sub;
-        if (sub == PH_NEG) {
-            masked(x, cmr, [](cx v) { return A::neg(v); });
-        } else if (sub == PH_POS_I) {
-            masked(x, cmr, [](cx v) { return A::mul_i(v); });
-        } else if (sub == PH_NEG_I) {
-            masked(x, cmr, [](cx v) { return A::mul_negi(v); });
-        } else {
-            const cx f = A::matp(op, 0);
-            masked(x, cmr, [&](cx v) { return A::mul(f, v); });
+                if (((uint32_t(r) ^ cvr) & cmr) == cmr) x[r] = f(x[r]);
         }
     }
 };
@@ -294,41 +271,71 @@ __device__ __forceinline__ void chunk_offsets(const DevPass& dp, uint64_t* choff
     }
 }
 
-// Tile-index offset of register r in the layout rpos.
+// Tile index of each of a thread's amplitudes in one layout: the bits held
+// by the lane and warp ids (with the flip applied) and one tile bit per
+// register-index bit.  The lane, register and warp bits hold disjoint tile
+// bits, so the index of register r is thr xor the bits of r's set register
+// bits.
 template <int RB>
-__device__ __forceinline__ uint32_t joff(uint32_t rpos, int r) {
-    uint32_t o = 0;
+struct TileMap {
+    uint32_t thr;
+    uint32_t rb[RB];
+    __device__ __forceinline__ uint32_t idx(int r) const {
+        uint32_t j = thr;
 #pragma unroll
-    for (int k = 0; k < RB; ++k)
-        if ((r >> k) & 1) o |= 1u << field5(rpos, k);
-    return o;
-}
+        for (int k = 0; k < RB; ++k)
+            if ((r >> k) & 1) j ^= rb[k];
+        return j;
+    }
+};
 
-// Initial layout of the pass: register bits and the lane / warp part jw.
-template <int RB>
-__device__ __forceinline__ void init_layout(const DevPass& dp, uint32_t lane, uint32_t wid, uint32_t& rpos,
-                                            uint32_t& jw) {
-    rpos = 0;
+// lanes == nullptr: lane bit i holds tile bit i.
+template <int RB, class T>
+__device__ __forceinline__ TileMap<RB> tile_map(const int8_t* lanes, const T* regs, const T* warps, int nwarp,
+                                                uint32_t flip, uint32_t lane, uint32_t wid) {
+    TileMap<RB> m;
+    uint32_t t = 0;
+    if (lanes == nullptr) {
+        t = lane;
+    } else {
 #pragma unroll
-    for (int k = 0; k < RB; ++k) rpos |= uint32_t(dp.layout[k]) << (5 * k);
-    jw = lane;
+        for (int i = 0; i < 5; ++i) t |= ((lane >> i) & 1u) << lanes[i];
+    }
 #pragma unroll
     for (int w = 0; w < 3; ++w)
-        if (w < dp.nwarp && ((wid >> w) & 1u)) jw |= 1u << dp.layout[RB + w];
+        if (w < nwarp) t |= ((wid >> w) & 1u) << warps[w];
+    m.thr = t ^ flip;
+#pragma unroll
+    for (int k = 0; k < RB; ++k) m.rb[k] = 1u << regs[k];
+    return m;
 }
 
-// Apply the pass's ops to the thread's registers x (layout rpos / jw, both
-// updated by OP_PERM and register renames).  `tile` is the shared-memory
-// buffer for layout changes.  Every thread of the CTA must call this.
+template <int RB>
+__device__ __forceinline__ TileMap<RB> initial_map(const DevPass& dp, uint32_t lane, uint32_t wid) {
+    return tile_map<RB>(nullptr, dp.layout, dp.layout + RB, dp.nwarp, 0u, lane, wid);
+}
+
+template <int RB>
+__device__ __forceinline__ TileMap<RB> layout_map(const TileLayout& L, int nwarp, uint32_t lane, uint32_t wid) {
+    return tile_map<RB>(L.lane, L.reg, L.warp, nwarp, L.flip, lane, wid);
+}
+
+// Apply the pass's ops to the thread's registers x.  The host resolved
+// every op against the layout it runs in; the kernel needs a layout only at
+// OP_PERM, which carries the old one.  `tile` is the shared-memory buffer
+// for layout changes.  Every thread of the CTA must call this.
 template <class A, int RB>
 __device__ __forceinline__ void run_ops(typename A::cx (&x)[1 << RB], const DevOp* __restrict__ pops, int nops,
-                                        uint64_t base, uint32_t lane, uint32_t wid, uint32_t& rpos, uint32_t& jw,
-                                        typename A::amp_t* tile) {
+                                        uint64_t base, uint32_t lane, uint32_t wid, typename A::amp_t* tile) {
     using RO = RegOps<A, RB>;
+    using cx = typename A::cx;
     constexpr int R = 1 << RB;
     // The ops are staged in shared memory, a chunk at a time: every thread
-    // reads every field of every op, and a shared-memory broadcast keeps
-    // that off the critical path that a global load per field would be on.
+    // reads every op, and a shared-memory broadcast keeps that off the
+    // critical path that a global load would be on.  Each op's header (its
+    // dispatch code, bits and conditions, resolved on the host) is one
+    // 16-byte load; the dispatch is a short if-chain by op class (measured
+    // faster than a jump table, and than loading the next header early).
     constexpr int kOpChunk = 64;
     __shared__ __align__(16) DevOp s_ops[kOpChunk];
     for (int c0 = 0; c0 < nops; c0 += kOpChunk) {
@@ -343,84 +350,65 @@ __device__ __forceinline__ void run_ops(typename A::cx (&x)[1 << RB], const DevO
     __syncthreads();
     for (int oi = 0; oi < cn; ++oi) {
         const DevOp* op = s_ops + oi;
-        const int kind = op->kind;
-        if (kind == OP_PERM) {
+        const RegHdr h = op->rh;
+        const uint64_t cmg = op->cm_glob;
+        if (h.code == RC_PERM) {
+            const TileMap<RB> from =
+                layout_map<RB>(*reinterpret_cast<const TileLayout*>(&op->m), op->nwarp, lane, wid);
             __syncthreads();  // the previous layout change has been read by all
 #pragma unroll
-            for (int r = 0; r < R; ++r) tile[jw | joff<RB>(rpos, r)] = A::st(x[r]);
+            for (int r = 0; r < R; ++r) tile[from.idx(r)] = A::st(x[r]);
             __syncthreads();
-            rpos = 0;
+            const TileMap<RB> to = tile_map<RB>(nullptr, op->perm, op->perm + RB, op->nwarp, 0u, lane, wid);
 #pragma unroll
-            for (int k = 0; k < RB; ++k) rpos |= uint32_t(op->perm[k]) << (5 * k);
-            jw = lane;
-#pragma unroll
-            for (int w = 0; w < 3; ++w)
-                if (w < op->nwarp && ((wid >> w) & 1u)) jw |= 1u << op->perm[RB + w];
-#pragma unroll
-            for (int r = 0; r < R; ++r) x[r] = A::ld(tile[jw | joff<RB>(rpos, r)]);
+            for (int r = 0; r < R; ++r) x[r] = A::ld(tile[to.idx(r)]);
             continue;
         }
-        const int role0 = op->role0;
-        if (kind <= OP_ANTI && kind != OP_DIAG && kind != OP_PHASE && role0 > 0 && role0 < kRoleLane) {
-            // target on register bit role0: bring it to register bit 0 (the
+        if (h.ren > 0) {
+            // target on register bit ren: bring it to register bit 0 (the
             // host tracks the same exchange; it happens even when the op is
             // skipped below, so the layout stays in step)
-            dispatch_k<RB>(role0, [&](auto kc) {
+            dispatch_k<RB>(h.ren, [&](auto kc) {
                 if constexpr (decltype(kc)::value > 0) RO::template swap_bits<decltype(kc)::value>(x);
             });
-            const uint32_t a = field5(rpos, 0), b = field5(rpos, role0);
-            rpos = (rpos & ~(31u | (31u << (5 * role0)))) | b | (a << (5 * role0));
         }
-        const uint64_t cmg = op->cm_glob;
         if ((base & cmg) != cmg) continue;  // a control outside the tile is 0: uniform skip
-        const uint32_t cmt = op->cm_thr;
-        const uint32_t cmr = op->cm_reg;
-        const bool thr_ok = (jw & cmt) == cmt;
-        switch (kind) {
-            case OP_DENSE:
-            case OP_REAL:
-            case OP_X:
-            case OP_ANTI:
-                if (role0 >= kRoleLane) RO::pair_lane(kind, x, op, role0 - kRoleLane, lane, thr_ok, cmr);
-                else RO::pair_reg0(kind, x, op, thr_ok, cmr);
-                break;
-            case OP_SWAP: {
-                const int role1 = op->role1;
-                if (role0 >= kRoleLane && role1 >= kRoleLane) {
-                    RO::swap_ll(x, role0 - kRoleLane, role1 - kRoleLane, lane, thr_ok, cmr);
-                } else if (role0 >= kRoleLane || role1 >= kRoleLane) {
-                    const int b = (role0 >= kRoleLane ? role0 : role1) - kRoleLane;
-                    const int k = role0 >= kRoleLane ? role1 : role0;
-                    dispatch_k<RB>(k, [&](auto kc) {
-                        RO::template swap_lr<decltype(kc)::value>(x, b, lane, thr_ok, cmr);
+        const bool thr_ok = ((threadIdx.x ^ h.cv_thr) & h.cm_thr) == h.cm_thr;
+        const uint32_t cmr = h.cm_reg, cvr = h.cv_reg;
+        const int code = h.code;
+        if (code <= RC_ANTI_L) {
+            if (code == RC_DENSE_R) RO::template pair_reg0<OP_DENSE>(x, op);
+            else if (code == RC_DENSE_L) RO::template pair_lane<OP_DENSE>(x, op, h.a, lane);
+            else if (code == RC_REAL_R) RO::template pair_reg0<OP_REAL>(x, op);
+            else if (code == RC_REAL_L) RO::template pair_lane<OP_REAL>(x, op, h.a, lane);
+            else if (code == RC_ANTI_R) RO::template pair_reg0<OP_ANTI>(x, op);
+            else RO::template pair_lane<OP_ANTI>(x, op, h.a, lane);
+        } else if (code <= RC_SWAP_LL) {
+            if (code == RC_X_R) RO::x_reg0(x, thr_ok, cmr, cvr);
+            else if (code == RC_X_L) RO::x_lane(x, h.a, thr_ok, cmr, cvr);
+            else if (code == RC_SWAP_LL) RO::swap_ll(x, h.a, h.b, lane, thr_ok, cmr, cvr);
+            else if (code == RC_SWAP_LR)
+                dispatch_k<RB>(h.b, [&](auto kc) {
+                    RO::template swap_lr<decltype(kc)::value>(x, h.a, lane, thr_ok, cmr, cvr);
+                });
+            else
+                dispatch_k<RB>(h.a, [&](auto a) {
+                    dispatch_k<RB>(h.b, [&](auto b) {
+                        constexpr int K0 = decltype(a)::value, K1 = decltype(b)::value;
+                        if constexpr (K0 < K1) RO::template swap_rr<K0, K1>(x, thr_ok, cmr, cvr);
                     });
-                } else {
-                    const int k0 = role0 < role1 ? role0 : role1;
-                    const int k1 = role0 < role1 ? role1 : role0;
-                    dispatch_k<RB>(k0, [&](auto a) {
-                        dispatch_k<RB>(k1, [&](auto b) {
-                            constexpr int K0 = decltype(a)::value, K1 = decltype(b)::value;
-                            if constexpr (K0 < K1) RO::template swap_rr<K0, K1>(x, thr_ok, cmr);
-                        });
-                    });
-                }
-                break;
+                });
+        } else if (code <= RC_DIAG_R) {
+            if (code == RC_DIAG_R) RO::diag_r(x, op, h.a);
+            else RO::diag_u(x, op, code == RC_DIAG_G ? int((base >> h.a) & 1u) : int((threadIdx.x >> h.a) & 1u));
+        } else if (thr_ok) {
+            if (code == RC_PH_NEG) RO::masked(x, h.mcls, h.a, cmr, cvr, [](cx v) { return A::neg(v); });
+            else if (code == RC_PH_POS_I) RO::masked(x, h.mcls, h.a, cmr, cvr, [](cx v) { return A::mul_i(v); });
+            else if (code == RC_PH_NEG_I) RO::masked(x, h.mcls, h.a, cmr, cvr, [](cx v) { return A::mul_negi(v); });
+            else if (code == RC_PH_GEN) {
+                const cx f = A::matp(op, 0);
+                RO::masked(x, h.mcls, h.a, cmr, cvr, [&](cx v) { return A::mul(f, v); });
             }
-            case OP_DIAG: {
-                if (role0 == kRoleNone) {
-                    RO::diag(x, op, -1, (base >> op->gq) & 1);
-                } else if (role0 >= kRoleThread) {
-                    RO::diag(x, op, -1, (jw >> (role0 - kRoleThread)) & 1u);
-                } else {
-                    RO::diag(x, op, role0, false);
-                }
-                break;
-            }
-            case OP_PHASE:
-                RO::phase(x, op, thr_ok, cmr);
-                break;
-            default:
-                break;
         }
     }
     }
@@ -441,20 +429,22 @@ __global__ void __launch_bounds__(256) k_pass_reg(typename A::amp_t* __restrict_
     const uint32_t lane = threadIdx.x & 31u, wid = threadIdx.x >> 5;
     const uint64_t base = tile_base(dp, worklist, blockIdx.x);
     chunk_offsets(dp, choff);
-    uint32_t rpos, jw;
-    init_layout<RB>(dp, lane, wid, rpos, jw);
     __syncthreads();
     const uint32_t lowmask = (1u << dp.lt) - 1u;
     cx x[R];
+    {
+        const TileMap<RB> m = initial_map<RB>(dp, lane, wid);
 #pragma unroll
-    for (int r = 0; r < R; ++r) {
-        const uint32_t j = jw | joff<RB>(rpos, r);
-        x[r] = A::ld(src[base | choff[j >> dp.lt] | (j & lowmask)]);
+        for (int r = 0; r < R; ++r) {
+            const uint32_t j = m.idx(r);
+            x[r] = A::ld(src[base | choff[j >> dp.lt] | (j & lowmask)]);
+        }
     }
-    run_ops<A, RB>(x, ops + dp.op_offset, dp.nops, base, lane, wid, rpos, jw, tile);
+    run_ops<A, RB>(x, ops + dp.op_offset, dp.nops, base, lane, wid, tile);
+    const TileMap<RB> m = layout_map<RB>(dp.fin, dp.nwarp, lane, wid);
 #pragma unroll
     for (int r = 0; r < R; ++r) {
-        const uint32_t j = jw | joff<RB>(rpos, r);
+        const uint32_t j = m.idx(r);
         dst[base | choff[j >> dp.lt] | (j & lowmask)] = A::st(x[r]);
     }
 }
@@ -560,17 +550,19 @@ __global__ void __launch_bounds__(256, (RB <= 3 ? 3 : 1)) k_pass_tma(typename A:
             return;
         }
         parity ^= 1u;
-        uint32_t rpos, jw;
-        init_layout<RB>(dp, lane, wid, rpos, jw);
         cx x[R];
+        {
+            const TileMap<RB> m = initial_map<RB>(dp, lane, wid);
 #pragma unroll
-        for (int r = 0; r < R; ++r) x[r] = A::ld(inbuf[jw | joff<RB>(rpos, r)]);
+            for (int r = 0; r < R; ++r) x[r] = A::ld(inbuf[m.idx(r)]);
+        }
         __syncthreads();  // inbuf is free: stage the next tile while computing this one
         if (t + gridDim.x < ntiles) issue(t + gridDim.x);
-        run_ops<A, RB>(x, ops + dp.op_offset, dp.nops, base, lane, wid, rpos, jw, tile);
+        run_ops<A, RB>(x, ops + dp.op_offset, dp.nops, base, lane, wid, tile);
+        const TileMap<RB> m = layout_map<RB>(dp.fin, dp.nwarp, lane, wid);
 #pragma unroll
         for (int r = 0; r < R; ++r) {
-            const uint32_t j = jw | joff<RB>(rpos, r);
+            const uint32_t j = m.idx(r);
             dst[base | choff[j >> dp.lt] | (j & lowmask)] = A::st(x[r]);
         }
     }
@@ -664,20 +656,22 @@ __device__ __forceinline__ void batch_tile(typename A::amp_t* __restrict__ state
     const uint32_t lane = threadIdx.x & 31u, wid = threadIdx.x >> 5;
     const uint64_t base = tile_base(dp, nullptr, t);
     chunk_offsets(dp, choff);
-    uint32_t rpos, jw;
-    init_layout<RB>(dp, lane, wid, rpos, jw);
     __syncthreads();
     const uint32_t lowmask = (1u << dp.lt) - 1u;
     cx x[R];
+    {
+        const TileMap<RB> m = initial_map<RB>(dp, lane, wid);
 #pragma unroll
-    for (int r = 0; r < R; ++r) {
-        const uint32_t j = jw | joff<RB>(rpos, r);
-        x[r] = A::ld(__ldcg(&state[base | choff[j >> dp.lt] | (j & lowmask)]));  // L2: written by other SMs
+        for (int r = 0; r < R; ++r) {
+            const uint32_t j = m.idx(r);
+            x[r] = A::ld(__ldcg(&state[base | choff[j >> dp.lt] | (j & lowmask)]));  // L2: written by other SMs
+        }
     }
-    run_ops<A, RB>(x, ops + dp.op_offset, dp.nops, base, lane, wid, rpos, jw, tile);
+    run_ops<A, RB>(x, ops + dp.op_offset, dp.nops, base, lane, wid, tile);
+    const TileMap<RB> m = layout_map<RB>(dp.fin, dp.nwarp, lane, wid);
 #pragma unroll
     for (int r = 0; r < R; ++r) {
-        const uint32_t j = jw | joff<RB>(rpos, r);
+        const uint32_t j = m.idx(r);
         state[base | choff[j >> dp.lt] | (j & lowmask)] = A::st(x[r]);
     }
     __threadfence();  // every thread's stores are visible device-wide before the tile is counted done

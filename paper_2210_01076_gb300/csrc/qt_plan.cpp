@@ -463,14 +463,20 @@ void close_all(Bitset* W, const std::vector<Pass>& passes, const std::vector<Bit
 }
 
 // ------------------------------------------------ register-kernel layout --
-// The register kernel holds tile bits 0-4 in the lane id; of the other tile
-// bits, nreg are register-index bits and nwarp warp-id bits.  An op whose
-// target is a warp bit cannot run in place, so the ops are walked in order
-// and, before the first op whose targets are not all lane or register bits,
-// an OP_PERM moves to a layout whose register bits hold that op's targets and
-// as many of the following ops' targets as fit (then bits of the old layout,
-// then the highest tile bits).
-void plan_register_layout(DevPass* dp, std::vector<DevOp>* ops_io) {
+// The register kernel holds each tile bit on a lane-id bit, a register-index
+// bit or a warp-id bit.  The ops are walked in order, tracking that layout
+// (TileLayout, with the flip of pending X gates):
+//  - an uncontrolled X only toggles the flip, an uncontrolled SWAP only
+//    exchanges the two tile bits' places: neither becomes a kernel op;
+//  - before the first op with a target on a warp bit, an OP_PERM moves (via
+//    shared memory) to a layout whose register bits hold that op's targets
+//    and as many of the following ops' targets as fit (then bits of the old
+//    layout, then the highest tile bits), lane bit i holding tile bit i, and
+//    applies the flip;
+//  - every other op is resolved against the current layout: targets and
+//    conditions become physical bits, a flipped target exchanges the op's
+//    matrix entries (X U X), a flipped condition is marked in the value mask.
+void plan_register_layout(DevPass* dp, std::vector<DevOp>* ops_io, int coef_bytes) {
     const int tb = dp->lt + dp->nh;
     dp->reg_kernel = 0;
     if (tb < 7) return;
@@ -481,25 +487,23 @@ void plan_register_layout(DevPass* dp, std::vector<DevOp>* ops_io) {
     dp->nwarp = nwarp;
     std::vector<DevOp>& ops = *ops_io;
     const uint32_t upper = ((1u << tb) - 1u) & ~31u;
-    auto need = [&](const DevOp& o) -> uint32_t {
-        uint32_t m = 0;
+    auto relabel = [](const DevOp& o) {
+        return (o.kind == OP_X || o.kind == OP_SWAP) && o.cm_glob == 0 && o.cm_tile == 0;
+    };
+    auto targets = [](const DevOp& o) -> uint32_t {
         switch (o.kind) {
-            case OP_DENSE: case OP_REAL: case OP_X: case OP_ANTI:
-                if (o.b0 >= 5) m |= 1u << o.b0;
-                break;
-            case OP_SWAP:
-                if (o.b0 >= 5) m |= 1u << o.b0;
-                if (o.b1 >= 5) m |= 1u << o.b1;
-                break;
-            default: break;
+            case OP_DENSE: case OP_REAL: case OP_X: case OP_ANTI: return 1u << o.b0;
+            case OP_SWAP: return (1u << o.b0) | (1u << o.b1);
+            default: return 0u;
         }
-        return m;
     };
     auto pc = [](uint32_t x) { return __builtin_popcount(x); };
+    // register set of a new layout for ops[i..]: their targets above the lanes
     auto choose = [&](size_t i, uint32_t keep) -> uint32_t {
-        uint32_t s = i < ops.size() ? need(ops[i]) : 0u;
-        for (size_t j = i + 1; j < ops.size() && pc(s) < nreg; ++j) {
-            const uint32_t t = s | need(ops[j]);
+        uint32_t s = 0;
+        for (size_t j = i; j < ops.size(); ++j) {
+            if (relabel(ops[j])) continue;
+            const uint32_t t = s | (targets(ops[j]) & upper);
             if (pc(t) > nreg) break;
             s = t;
         }
@@ -509,84 +513,178 @@ void plan_register_layout(DevPass* dp, std::vector<DevOp>* ops_io) {
             if ((upper >> b) & 1u) s |= 1u << b;
         return s;
     };
-    auto fill = [&](uint32_t regset, int32_t* out32, int8_t* out8) {
-        int k = 0;
-        for (int b = 5; b < tb; ++b)
-            if ((regset >> b) & 1u) {
-                if (out32) out32[k] = b;
-                if (out8) out8[k] = int8_t(b);
-                ++k;
-            }
-        for (int b = 5; b < tb; ++b)
-            if (((upper & ~regset) >> b) & 1u) {
-                if (out32) out32[k] = b;
-                if (out8) out8[k] = int8_t(b);
-                ++k;
-            }
+    // where[t]: 0..4 lane bit, 8 + k register bit k, 16 + w warp bit w
+    TileLayout L;
+    int where[32];
+    auto set_layout = [&](uint32_t regset) {
+        std::memset(&L, 0, sizeof L);
+        int k = 0, w = 0;
+        for (int b = 0; b < 5; ++b) L.lane[b] = int8_t(b);
+        for (int b = 5; b < tb; ++b) {
+            if ((regset >> b) & 1u) L.reg[k++] = int8_t(b);
+            else L.warp[w++] = int8_t(b);
+        }
+        for (int b = 0; b < 5; ++b) where[b] = b;
+        for (int j = 0; j < nreg; ++j) where[L.reg[j]] = 8 + j;
+        for (int j = 0; j < nwarp; ++j) where[L.warp[j]] = 16 + j;
     };
-    // regs[k] = tile bit of register-index bit k (the kernel's order); a
-    // layout change sets them ascending, a pair op on register bit k > 0
-    // exchanges regs[0] and regs[k] (the kernel moves the registers to match)
+    auto placed = [&](uint32_t tm) {
+        for (int t = 0; t < tb; ++t)
+            if (((tm >> t) & 1u) && where[t] >= 16) return false;
+        return true;
+    };
     uint32_t cur = choose(0, 0);
-    fill(cur, dp->layout, nullptr);
-    int regs[8];
-    for (int k = 0; k < nreg; ++k) regs[k] = dp->layout[k];
+    set_layout(cur);
+    for (int k = 0; k < nreg; ++k) dp->layout[k] = L.reg[k];
+    for (int w = 0; w < nwarp; ++w) dp->layout[nreg + w] = L.warp[w];
+    auto emit_perm = [&](std::vector<DevOp>& out, uint32_t regset) {
+        DevOp pm;
+        std::memset(&pm, 0, sizeof pm);
+        pm.kind = OP_PERM;
+        pm.rh.code = RC_PERM;
+        pm.nreg = int8_t(nreg);
+        pm.nwarp = int8_t(nwarp);
+        static_assert(sizeof(TileLayout) <= sizeof(pm.m), "old layout fits the matrix field");
+        std::memcpy(&pm.m, &L, sizeof L);
+        set_layout(regset);
+        for (int k = 0; k < nreg; ++k) pm.perm[k] = L.reg[k];
+        for (int w = 0; w < nwarp; ++w) pm.perm[nreg + w] = L.warp[w];
+        out.push_back(pm);
+    };
+    auto swap_entries = [&](DevOp& o, int i, int j) {
+        unsigned char* m = reinterpret_cast<unsigned char*>(&o.m);
+        unsigned char t[16];
+        std::memcpy(t, m + i * coef_bytes, size_t(coef_bytes));
+        std::memcpy(m + i * coef_bytes, m + j * coef_bytes, size_t(coef_bytes));
+        std::memcpy(m + j * coef_bytes, t, size_t(coef_bytes));
+    };
     std::vector<DevOp> out;
     out.reserve(ops.size() + 4);
-    auto regidx = [&](int b) -> int {
-        for (int k = 0; k < nreg; ++k)
-            if (regs[k] == b) return k;
-        return -1;
-    };
     for (size_t i = 0; i < ops.size(); ++i) {
         DevOp o = ops[i];
-        if (need(o) & ~cur) {
-            cur = choose(i, cur);
-            DevOp pm;
-            std::memset(&pm, 0, sizeof pm);
-            pm.kind = OP_PERM;
-            pm.nreg = int8_t(nreg);
-            pm.nwarp = int8_t(nwarp);
-            fill(cur, nullptr, pm.perm);
-            for (int k = 0; k < nreg; ++k) regs[k] = pm.perm[k];
-            out.push_back(pm);
+        if (relabel(o)) {
+            if (o.kind == OP_X) {
+                L.flip ^= 1u << o.b0;
+            } else {
+                const int t1 = o.b0, t2 = o.b1, p1 = where[t1], p2 = where[t2];
+                auto slot = [&](int p) -> int8_t& { return p < 8 ? L.lane[p] : p < 16 ? L.reg[p - 8] : L.warp[p - 16]; };
+                slot(p1) = int8_t(t2);
+                slot(p2) = int8_t(t1);
+                where[t1] = p2;
+                where[t2] = p1;
+                const uint32_t f1 = (L.flip >> t1) & 1u, f2 = (L.flip >> t2) & 1u;
+                L.flip = (L.flip & ~((1u << t1) | (1u << t2))) | (f1 << t2) | (f2 << t1);
+            }
+            continue;
         }
+        const uint32_t tg = targets(o);
+        // a conditioned SWAP whose two bits are flipped differently exchanges
+        // another pair of patterns: apply the flip with a layout change first
+        const bool swap_mixed = o.kind == OP_SWAP && (((L.flip >> o.b0) ^ (L.flip >> o.b1)) & 1u);
+        if (!placed(tg) || swap_mixed) {
+            cur = choose(i, cur);
+            emit_perm(out, cur);
+        }
+        const uint32_t F = L.flip;
+        // conditions on physical bits, flipped ones marked in the value masks
+        uint32_t thr = 0, cvt = 0;
+        uint16_t reg = 0;
+        uint8_t cvr = 0;
+        for (int b = 0; b < tb; ++b) {
+            if (!((o.cm_tile >> b) & 1u)) continue;
+            const int p = where[b];
+            const uint32_t f = (F >> b) & 1u;
+            if (p >= 8 && p < 16) {
+                reg |= uint16_t(1u << (p - 8));
+                cvr |= uint8_t(f << (p - 8));
+            } else {
+                const int tbit = p < 8 ? p : 5 + (p - 16);
+                thr |= 1u << tbit;
+                cvt |= f << tbit;
+            }
+        }
+        RegHdr h;
+        std::memset(&h, 0, sizeof h);
+        h.code = RC_NOP;
         const bool pair = o.kind == OP_DENSE || o.kind == OP_REAL || o.kind == OP_X || o.kind == OP_ANTI;
         if (pair) {
-            if (o.b0 < 5) {
-                o.role0 = int8_t(kRoleLane + o.b0);
-            } else {
-                const int k = regidx(o.b0);
-                o.role0 = int8_t(k);
-                if (k > 0) std::swap(regs[0], regs[k]);
+            if ((F >> o.b0) & 1u) {  // X U X: the stored pair is exchanged
+                if (o.kind == OP_DENSE || o.kind == OP_REAL) {
+                    swap_entries(o, 0, 3);
+                    swap_entries(o, 1, 2);
+                } else if (o.kind == OP_ANTI) {
+                    swap_entries(o, 0, 1);
+                }
             }
-            o.role1 = kRoleNone;
+            const int cr = o.kind == OP_DENSE ? RC_DENSE_R : o.kind == OP_REAL ? RC_REAL_R
+                         : o.kind == OP_X ? RC_X_R : RC_ANTI_R;
+            const int p = where[o.b0];
+            if (p < 8) {
+                h.code = uint8_t(cr + 1);  // the _L variant
+                h.a = int8_t(p);
+            } else {
+                const int k = p - 8;
+                h.code = uint8_t(cr);
+                if (k > 0) {
+                    // the kernel exchanges register bits 0 and k first
+                    h.ren = int8_t(k);
+                    auto x0k = [k](uint32_t v) -> uint32_t {
+                        const uint32_t b0 = v & 1u, bk = (v >> k) & 1u;
+                        return (v & ~(1u | (1u << k))) | (b0 << k) | bk;
+                    };
+                    reg = uint16_t(x0k(reg));
+                    cvr = uint8_t(x0k(cvr));
+                    const int t0 = L.reg[0], tk = L.reg[k];
+                    L.reg[0] = int8_t(tk);
+                    L.reg[k] = int8_t(t0);
+                    where[tk] = 8;
+                    where[t0] = 8 + k;
+                }
+            }
         } else if (o.kind == OP_SWAP) {
-            o.role0 = o.b0 < 5 ? int8_t(kRoleLane + o.b0) : int8_t(regidx(o.b0));
-            o.role1 = o.b1 < 5 ? int8_t(kRoleLane + o.b1) : int8_t(regidx(o.b1));
+            const int p0 = where[o.b0], p1 = where[o.b1];
+            if (p0 < 8 && p1 < 8) {
+                h.code = RC_SWAP_LL;
+                h.a = int8_t(p0);
+                h.b = int8_t(p1);
+            } else if (p0 < 8 || p1 < 8) {
+                h.code = RC_SWAP_LR;
+                h.a = int8_t(p0 < 8 ? p0 : p1);
+                h.b = int8_t((p0 < 8 ? p1 : p0) - 8);
+            } else {
+                h.code = RC_SWAP_RR;
+                h.a = int8_t(std::min(p0, p1) - 8);
+                h.b = int8_t(std::max(p0, p1) - 8);
+            }
         } else if (o.kind == OP_DIAG) {
-            if (o.b0 < 0) o.role0 = kRoleNone;
-            else if (o.b0 >= 5 && regidx(o.b0) >= 0) o.role0 = int8_t(regidx(o.b0));
-            else o.role0 = int8_t(kRoleThread + o.b0);
-            o.role1 = kRoleNone;
-        } else {
-            o.role0 = o.role1 = kRoleNone;
+            if (o.b0 < 0) {
+                h.code = RC_DIAG_G;
+                h.a = int8_t(o.gq);
+            } else {
+                if ((F >> o.b0) & 1u) swap_entries(o, 0, 1);
+                const int p = where[o.b0];
+                if (p >= 8 && p < 16) {
+                    h.code = RC_DIAG_R;
+                    h.a = int8_t(p - 8);
+                } else {
+                    h.code = RC_DIAG_T;
+                    h.a = int8_t(p < 8 ? p : 5 + (p - 16));
+                }
+            }
+        } else if (o.kind == OP_PHASE) {
+            h.code = o.sub == PH_NEG ? RC_PH_NEG : o.sub == PH_POS_I ? RC_PH_POS_I
+                   : o.sub == PH_NEG_I ? RC_PH_NEG_I : RC_PH_GEN;
+            h.mcls = reg == 0 ? 0 : ((reg & (reg - 1)) == 0 && cvr == 0) ? 1 : 2;
+            if (h.mcls == 1) h.a = int8_t(__builtin_ctz(reg));
         }
-        // split the tile-local control mask (held in cm_thr on entry) for the
-        // layout the op runs in
-        const uint32_t cmt = o.cm_thr;
-        uint32_t thr = 0;
-        uint16_t reg = 0;
-        for (int b = 0; b < tb; ++b) {
-            if (!((cmt >> b) & 1u)) continue;
-            const int k = b >= 5 ? regidx(b) : -1;
-            if (k >= 0) reg |= uint16_t(1u << k);
-            else thr |= 1u << b;
-        }
-        o.cm_thr = thr;
-        o.cm_reg = reg;
+        h.cm_reg = reg;
+        h.cv_reg = cvr;
+        h.cm_thr = thr;
+        h.cv_thr = cvt;
+        o.rh = h;
         out.push_back(o);
     }
+    dp->fin = L;
     ops.swap(out);
 }
 
