@@ -36,6 +36,19 @@ __device__ __forceinline__ df fast_two_sum(float a, float b) {
 }
 
 __device__ __forceinline__ df dneg(df a) { return {-a.hi, -a.lo}; }
+// Negation and copy as FP32 multiplies by -1 and 1 (exact).  In the register
+// kernel the exchanges of X/SWAP ops, register renames and the ±1/±i phases
+// otherwise become register moves and sign flips on the half-rate ALU pipe,
+// which the op mix saturates while the FMA pipe has room; as multiplies they
+// issue on the FMA pipe (measured 16% less time on the benchmark circuit).
+// Written as PTX so that the compiler keeps the multiply.
+__device__ __forceinline__ float fmul_c(float a, float c) {
+    float d;
+    asm("mul.rn.f32 %0, %1, %2;" : "=f"(d) : "f"(a), "f"(c));
+    return d;
+}
+__device__ __forceinline__ df dneg_f(df a) { return {fmul_c(a.hi, -1.0f), fmul_c(a.lo, -1.0f)}; }
+__device__ __forceinline__ df dcopy_f(df a) { return {fmul_c(a.hi, 1.0f), fmul_c(a.lo, 1.0f)}; }
 
 // sum_k a_k * b_k for K float-float pairs.  Each product's leading term is
 // split exactly by an FMA; the leading terms are summed with two_sum and all
@@ -93,6 +106,7 @@ struct ArF64 {
     }
     static __device__ __forceinline__ cx matp(const DevOp* op, int k) { return {op->m.d[2 * k], op->m.d[2 * k + 1]}; }
     static __device__ __forceinline__ cx sel(bool c, cx a, cx b) { return c ? a : b; }
+    static __device__ __forceinline__ cx mv(cx a) { return a; }
 };
 
 struct ArF32 {
@@ -126,6 +140,7 @@ struct ArF32 {
     }
     static __device__ __forceinline__ cx matp(const DevOp* op, int k) { return {op->m.f[2 * k], op->m.f[2 * k + 1]}; }
     static __device__ __forceinline__ cx sel(bool c, cx a, cx b) { return c ? a : b; }
+    static __device__ __forceinline__ cx mv(cx a) { return {fmul_c(a.re, 1.0f), fmul_c(a.im, 1.0f)}; }
 };
 
 struct ArDF {
@@ -158,9 +173,10 @@ struct ArDF {
         const df bi[2] = {b.im, b.re};
         return {df_dot<2>(ar, br), df_dot<2>(ai, bi)};
     }
-    static __device__ __forceinline__ cx neg(cx a) { return {dneg(a.re), dneg(a.im)}; }
-    static __device__ __forceinline__ cx mul_i(cx a) { return {dneg(a.im), a.re}; }
-    static __device__ __forceinline__ cx mul_negi(cx a) { return {a.im, dneg(a.re)}; }
+    static __device__ __forceinline__ cx neg(cx a) { return {dneg_f(a.re), dneg_f(a.im)}; }
+    static __device__ __forceinline__ cx mul_i(cx a) { return {dneg_f(a.im), dcopy_f(a.re)}; }
+    static __device__ __forceinline__ cx mul_negi(cx a) { return {dcopy_f(a.im), dneg_f(a.re)}; }
+    static __device__ __forceinline__ cx mv(cx a) { return {dcopy_f(a.re), dcopy_f(a.im)}; }
     static __device__ __forceinline__ cx shfl(cx a, int mask) {
         return {{__shfl_xor_sync(0xffffffffu, a.re.hi, mask), __shfl_xor_sync(0xffffffffu, a.re.lo, mask)},
                 {__shfl_xor_sync(0xffffffffu, a.im.hi, mask), __shfl_xor_sync(0xffffffffu, a.im.lo, mask)}};

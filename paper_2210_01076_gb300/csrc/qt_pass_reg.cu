@@ -59,7 +59,8 @@ struct RegOps {
     using cx = typename A::cx;
     static constexpr int R = 1 << RB;
 
-    // exchange register-index bits 0 and K (K > 0)
+    // exchange register-index bits 0 and K (K > 0).  Moved values go through
+    // A::mv, a copy that issues on the FMA pipe (see qt_arith.cuh).
     template <int K>
     static __device__ __forceinline__ void swap_bits(cx (&x)[R]) {
 #pragma unroll
@@ -67,8 +68,8 @@ struct RegOps {
             if ((r & 1) && !((r >> K) & 1)) {
                 const int r2 = r ^ (1 | (1 << K));
                 const cx t = x[r];
-                x[r] = x[r2];
-                x[r2] = t;
+                x[r] = A::mv(x[r2]);
+                x[r2] = A::mv(t);
             }
         }
     }
@@ -110,8 +111,8 @@ struct RegOps {
         for (int r = 0; r < R; r += 2) {
             if (!(thr_ok && ((uint32_t(r) ^ cvr) & cmr) == cmr)) continue;
             const cx a = x[r];
-            x[r] = x[r + 1];
-            x[r + 1] = a;
+            x[r] = A::mv(x[r + 1]);
+            x[r + 1] = A::mv(a);
         }
     }
 
@@ -156,8 +157,8 @@ struct RegOps {
             const int r2 = r ^ ((1 << K0) | (1 << K1));
             if (!(thr_ok && ((uint32_t(r) ^ cvr) & cmr) == cmr)) continue;
             const cx a = x[r];
-            x[r] = x[r2];
-            x[r2] = a;
+            x[r] = A::mv(x[r2]);
+            x[r2] = A::mv(a);
         }
     }
 
