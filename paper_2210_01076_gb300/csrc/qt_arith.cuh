@@ -132,9 +132,9 @@ struct ArF32 {
     static __device__ __forceinline__ cx mul(cx a, cx b) {
         return {__fmaf_rn(a.re, b.re, __fmul_rn(-a.im, b.im)), __fmaf_rn(a.re, b.im, __fmul_rn(a.im, b.re))};
     }
-    static __device__ __forceinline__ cx neg(cx a) { return {-a.re, -a.im}; }
-    static __device__ __forceinline__ cx mul_i(cx a) { return {-a.im, a.re}; }
-    static __device__ __forceinline__ cx mul_negi(cx a) { return {a.im, -a.re}; }
+    static __device__ __forceinline__ cx neg(cx a) { return {fmul_c(a.re, -1.0f), fmul_c(a.im, -1.0f)}; }
+    static __device__ __forceinline__ cx mul_i(cx a) { return {fmul_c(a.im, -1.0f), fmul_c(a.re, 1.0f)}; }
+    static __device__ __forceinline__ cx mul_negi(cx a) { return {fmul_c(a.im, 1.0f), fmul_c(a.re, -1.0f)}; }
     static __device__ __forceinline__ cx shfl(cx a, int mask) {
         return {__shfl_xor_sync(0xffffffffu, a.re, mask), __shfl_xor_sync(0xffffffffu, a.im, mask)};
     }
