@@ -67,7 +67,7 @@ double op_alu_per_amp(int dtype, const HostOp& op) {
     const bool df = dtype == QT_C128_DF;
     switch (op.kind) {
         case OP_DENSE: return df ? 86.0 : 8.0;
-        case OP_REAL: case OP_DIAG: case OP_ANTI: return df ? 38.0 : 4.0;
+        case OP_REAL: case OP_IREAL: case OP_DIAG: case OP_ANTI: return df ? 38.0 : 4.0;
         case OP_PHASE: {
             const bool exact = (op.m[0] == -1.0 && op.m[1] == 0.0) || (op.m[0] == 0.0 && (op.m[1] == 1.0 || op.m[1] == -1.0));
             if (exact) return 0.0;
@@ -350,7 +350,7 @@ DevOp encode_op(int dtype, const Pass& ps, const HostOp& op) {
     d.gq = op.q0;
     d.b1 = -1;
     switch (op.kind) {
-        case OP_DENSE: case OP_REAL: case OP_X: case OP_ANTI:
+        case OP_DENSE: case OP_REAL: case OP_IREAL: case OP_X: case OP_ANTI:
             fixed.push_back({d.b0, 0});
             break;
         case OP_SWAP:

@@ -95,6 +95,13 @@ struct ArF64 {
         r.im = __fma_rn(u0.re, x0.im, __dmul_rn(u1.re, x1.im));
         return r;
     }
+    // u0 x0 + u1 x1 with u0 real and u1 imaginary (OP_IREAL)
+    static __device__ __forceinline__ cx lin2i(cx u0, cx x0, cx u1, cx x1) {
+        cx r;
+        r.re = __fma_rn(u0.re, x0.re, __dmul_rn(-u1.im, x1.im));
+        r.im = __fma_rn(u0.re, x0.im, __dmul_rn(u1.im, x1.re));
+        return r;
+    }
     static __device__ __forceinline__ cx mul(cx a, cx b) {
         return {__fma_rn(a.re, b.re, __dmul_rn(-a.im, b.im)), __fma_rn(a.re, b.im, __dmul_rn(a.im, b.re))};
     }
@@ -127,6 +134,12 @@ struct ArF32 {
         cx r;
         r.re = __fmaf_rn(u0.re, x0.re, __fmul_rn(u1.re, x1.re));
         r.im = __fmaf_rn(u0.re, x0.im, __fmul_rn(u1.re, x1.im));
+        return r;
+    }
+    static __device__ __forceinline__ cx lin2i(cx u0, cx x0, cx u1, cx x1) {
+        cx r;
+        r.re = __fmaf_rn(u0.re, x0.re, __fmul_rn(-u1.im, x1.im));
+        r.im = __fmaf_rn(u0.re, x0.im, __fmul_rn(u1.im, x1.re));
         return r;
     }
     static __device__ __forceinline__ cx mul(cx a, cx b) {
@@ -165,6 +178,13 @@ struct ArDF {
         const df br[2] = {x0.re, x1.re};
         const df bi[2] = {x0.im, x1.im};
         return {df_dot<2>(a, br), df_dot<2>(a, bi)};
+    }
+    static __device__ __forceinline__ cx lin2i(cx u0, cx x0, cx u1, cx x1) {
+        const df ar[2] = {u0.re, dneg(u1.im)};
+        const df br[2] = {x0.re, x1.im};
+        const df ai[2] = {u0.re, u1.im};
+        const df bi[2] = {x0.im, x1.re};
+        return {df_dot<2>(ar, br), df_dot<2>(ai, bi)};
     }
     static __device__ __forceinline__ cx mul(cx a, cx b) {
         const df ar[2] = {a.re, dneg(a.im)};

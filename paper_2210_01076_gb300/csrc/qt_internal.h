@@ -26,6 +26,8 @@ enum OpKind : int32_t {
     OP_X = 4,      // exchange the pair on target q0
     OP_ANTI = 5,   // [[0, m01], [m10, 0]] on target q0 (Y and fused permutation-phases)
     OP_SWAP = 6,   // exchange amplitudes with (q0, q1) bits (1,0) and (0,1)
+    // (7 is OP_PERM, a register-kernel layout change)
+    OP_IREAL = 8,  // [[a, ib], [ic, d]] with a, b, c, d real on target q0 (RX and its products)
 };
 
 // Phase sub-kinds, chosen on the host so that exact factors cost no rounding.
@@ -156,6 +158,7 @@ enum RegCode : uint8_t {
     RC_DENSE_R, RC_DENSE_L,  // _R: target on register bit 0, _L: on lane bit a
     RC_REAL_R, RC_REAL_L,
     RC_ANTI_R, RC_ANTI_L,
+    RC_IREAL_R, RC_IREAL_L,
     RC_X_R, RC_X_L,
     RC_SWAP_RR,  // register bits a < b
     RC_SWAP_LR,  // lane bit a, register bit b

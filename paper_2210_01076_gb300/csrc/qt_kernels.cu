@@ -76,6 +76,17 @@ __device__ __forceinline__ void apply_op(typename A::amp_t* tile, uint32_t tb, c
             }
             break;
         }
+        case OP_IREAL: {
+            const cx u00 = A::mat(op, 0), u01 = A::mat(op, 1), u10 = A::mat(op, 2), u11 = A::mat(op, 3);
+            const uint32_t tbit = 1u << op.b0;
+            for (uint32_t k = threadIdx.x; k < iters; k += blockDim.x) {
+                const uint32_t i0 = expand_fixed(k, op), i1 = i0 | tbit;
+                const cx x0 = A::ld(tile[i0]), x1 = A::ld(tile[i1]);
+                tile[i0] = A::st(A::lin2i(u00, x0, u01, x1));
+                tile[i1] = A::st(A::lin2i(u11, x1, u10, x0));
+            }
+            break;
+        }
         case OP_X: {
             const uint32_t tbit = 1u << op.b0;
             for (uint32_t k = threadIdx.x; k < iters; k += blockDim.x) {

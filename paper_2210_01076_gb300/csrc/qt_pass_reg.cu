@@ -74,8 +74,8 @@ struct RegOps {
         }
     }
 
-    // one-target ops on register bit 0: pairs (x[2i], x[2i+1]).  DENSE, REAL
-    // and ANTI ops never carry conditions (only X, SWAP and PHASE do; the
+    // one-target ops on register bit 0: pairs (x[2i], x[2i+1]).  DENSE, REAL,
+    // IREAL and ANTI ops never carry conditions (only X, SWAP and PHASE do; the
     // host checks it), so their loops need no per-amplitude predicate.
     template <int KIND>
     static __device__ __forceinline__ void pair_reg0(cx (&x)[R], const DevOp* op) {
@@ -94,6 +94,14 @@ struct RegOps {
                 const cx a = x[r], b = x[r + 1];
                 x[r] = A::lin2r(u00, a, u01, b);
                 x[r + 1] = A::lin2r(u10, a, u11, b);
+            }
+        } else if constexpr (KIND == OP_IREAL) {
+            const cx u00 = A::matp(op, 0), u01 = A::matp(op, 1), u10 = A::matp(op, 2), u11 = A::matp(op, 3);
+#pragma unroll
+            for (int r = 0; r < R; r += 2) {
+                const cx a = x[r], b = x[r + 1];
+                x[r] = A::lin2i(u00, a, u01, b);
+                x[r + 1] = A::lin2i(u11, b, u10, a);
             }
         } else {  // OP_ANTI
             const cx m01 = A::matp(op, 0), m10 = A::matp(op, 1);
@@ -123,14 +131,15 @@ struct RegOps {
     static __device__ __forceinline__ void pair_lane(cx (&x)[R], const DevOp* op, int b, uint32_t lane) {
         const int mask = 1 << b;
         const int hi = int((lane >> b) & 1u);
-        if constexpr (KIND == OP_DENSE || KIND == OP_REAL) {
+        if constexpr (KIND == OP_DENSE || KIND == OP_REAL || KIND == OP_IREAL) {
             const cx cs = A::sel(hi, A::matp(op, 3), A::matp(op, 0));
             const cx cp = A::sel(hi, A::matp(op, 2), A::matp(op, 1));
 #pragma unroll
             for (int r = 0; r < R; ++r) {
                 const cx p = A::shfl(x[r], mask);
                 if constexpr (KIND == OP_DENSE) x[r] = A::lin2(cs, x[r], cp, p);
-                else x[r] = A::lin2r(cs, x[r], cp, p);
+                else if constexpr (KIND == OP_REAL) x[r] = A::lin2r(cs, x[r], cp, p);
+                else x[r] = A::lin2i(cs, x[r], cp, p);
             }
         } else {  // OP_ANTI: bit-0 output m01 a1, bit-1 output m10 a0
             const cx c = A::sel(hi, A::matp(op, 1), A::matp(op, 0));
@@ -377,13 +386,15 @@ __device__ __forceinline__ void run_ops(typename A::cx (&x)[1 << RB], const DevO
         const bool thr_ok = ((threadIdx.x ^ h.cv_thr) & h.cm_thr) == h.cm_thr;
         const uint32_t cmr = h.cm_reg, cvr = h.cv_reg;
         const int code = h.code;
-        if (code <= RC_ANTI_L) {
+        if (code <= RC_IREAL_L) {
             if (code == RC_DENSE_R) RO::template pair_reg0<OP_DENSE>(x, op);
             else if (code == RC_DENSE_L) RO::template pair_lane<OP_DENSE>(x, op, h.a, lane);
             else if (code == RC_REAL_R) RO::template pair_reg0<OP_REAL>(x, op);
             else if (code == RC_REAL_L) RO::template pair_lane<OP_REAL>(x, op, h.a, lane);
             else if (code == RC_ANTI_R) RO::template pair_reg0<OP_ANTI>(x, op);
-            else RO::template pair_lane<OP_ANTI>(x, op, h.a, lane);
+            else if (code == RC_ANTI_L) RO::template pair_lane<OP_ANTI>(x, op, h.a, lane);
+            else if (code == RC_IREAL_R) RO::template pair_reg0<OP_IREAL>(x, op);
+            else RO::template pair_lane<OP_IREAL>(x, op, h.a, lane);
         } else if (code <= RC_SWAP_LL) {
             if (code == RC_X_R) RO::x_reg0(x, thr_ok, cmr, cvr);
             else if (code == RC_X_L) RO::x_lane(x, h.a, thr_ok, cmr, cvr);

@@ -112,7 +112,9 @@ HostOp classify(const M2& U, int q, uint64_t cmask, int ngates) {
     }
     bool real = true;
     for (int k = 0; k < 4; ++k) real = real && a[k].imag() == 0.0;
-    op.kind = real ? OP_REAL : OP_DENSE;
+    // real diagonal, imaginary off-diagonal (RX): as cheap as a real 2x2
+    const bool ireal = a[0].imag() == 0.0 && a[3].imag() == 0.0 && a[1].real() == 0.0 && a[2].real() == 0.0;
+    op.kind = real ? OP_REAL : ireal ? OP_IREAL : OP_DENSE;
     for (int k = 0; k < 4; ++k) put(op.m, k, a[k]);
     return op;
 }
@@ -121,7 +123,7 @@ bool op_matrix(const HostOp& op, M2* U) {
     cd* a = U->a;
     a[0] = a[1] = a[2] = a[3] = 0.0;
     switch (op.kind) {
-        case OP_DENSE: case OP_REAL:
+        case OP_DENSE: case OP_REAL: case OP_IREAL:
             for (int k = 0; k < 4; ++k) a[k] = get(op.m, k);
             return true;
         case OP_DIAG: a[0] = get(op.m, 0); a[3] = get(op.m, 1); return true;
@@ -159,7 +161,7 @@ int popcount64(uint64_t x) { return __builtin_popcountll(x); }
 int op_cost(const HostOp& op) {
     switch (op.kind) {
         case OP_DENSE: return 86;
-        case OP_REAL: case OP_DIAG: case OP_ANTI: return 38;
+        case OP_REAL: case OP_IREAL: case OP_DIAG: case OP_ANTI: return 38;
         case OP_PHASE: {
             const bool exact = (op.m[0] == -1.0 && op.m[1] == 0.0) || (op.m[0] == 0.0 && std::fabs(op.m[1]) == 1.0);
             return exact ? 4 : 38;
@@ -226,24 +228,6 @@ bool lower_gate(const qt_gate& g, int n, std::vector<HostOp>* out, std::string* 
     }
     uint64_t cmask = 0;
     for (int k = 0; k < g.ncontrol; ++k) cmask |= uint64_t(1) << g.control[k];
-    if (g.kind == QT_RX && cmask == 0) {
-        // A complex 2x2 costs about twice a real one; RX is a real rotation
-        // between two exact phases (a multiply by +-i only moves data):
-        //   RX(t) = diag(1, -i) RY(t) diag(1, i)
-        const double t = g.theta[0];
-        const double c = std::cos(t / 2.0), s = std::sin(t / 2.0);
-        const cd I(0.0, 1.0);
-        const cd first = I;
-        const cd last = -I;
-        M2 P1, RY, P2;
-        P1.a[0] = 1.0; P1.a[1] = 0.0; P1.a[2] = 0.0; P1.a[3] = first;
-        RY.a[0] = c; RY.a[1] = -s; RY.a[2] = s; RY.a[3] = c;
-        P2.a[0] = 1.0; P2.a[1] = 0.0; P2.a[2] = 0.0; P2.a[3] = last;
-        out->push_back(classify(P1, g.target[0], 0, 0));
-        out->push_back(classify(RY, g.target[0], 0, 1));
-        out->push_back(classify(P2, g.target[0], 0, 0));
-        return true;
-    }
     out->push_back(classify(U, g.target[0], cmask, 1));
     return true;
 }
@@ -492,7 +476,7 @@ void plan_register_layout(DevPass* dp, std::vector<DevOp>* ops_io, int coef_byte
     };
     auto targets = [](const DevOp& o) -> uint32_t {
         switch (o.kind) {
-            case OP_DENSE: case OP_REAL: case OP_X: case OP_ANTI: return 1u << o.b0;
+            case OP_DENSE: case OP_REAL: case OP_IREAL: case OP_X: case OP_ANTI: return 1u << o.b0;
             case OP_SWAP: return (1u << o.b0) | (1u << o.b1);
             default: return 0u;
         }
@@ -606,10 +590,11 @@ void plan_register_layout(DevPass* dp, std::vector<DevOp>* ops_io, int coef_byte
         RegHdr h;
         std::memset(&h, 0, sizeof h);
         h.code = RC_NOP;
-        const bool pair = o.kind == OP_DENSE || o.kind == OP_REAL || o.kind == OP_X || o.kind == OP_ANTI;
+        const bool pair = o.kind == OP_DENSE || o.kind == OP_REAL || o.kind == OP_IREAL || o.kind == OP_X ||
+                          o.kind == OP_ANTI;
         if (pair) {
             if ((F >> o.b0) & 1u) {  // X U X: the stored pair is exchanged
-                if (o.kind == OP_DENSE || o.kind == OP_REAL) {
+                if (o.kind == OP_DENSE || o.kind == OP_REAL || o.kind == OP_IREAL) {
                     swap_entries(o, 0, 3);
                     swap_entries(o, 1, 2);
                 } else if (o.kind == OP_ANTI) {
@@ -617,7 +602,7 @@ void plan_register_layout(DevPass* dp, std::vector<DevOp>* ops_io, int coef_byte
                 }
             }
             const int cr = o.kind == OP_DENSE ? RC_DENSE_R : o.kind == OP_REAL ? RC_REAL_R
-                         : o.kind == OP_X ? RC_X_R : RC_ANTI_R;
+                         : o.kind == OP_IREAL ? RC_IREAL_R : o.kind == OP_X ? RC_X_R : RC_ANTI_R;
             const int p = where[o.b0];
             if (p < 8) {
                 h.code = uint8_t(cr + 1);  // the _L variant
