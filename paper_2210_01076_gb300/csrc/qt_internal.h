@@ -235,7 +235,9 @@ struct DevPass {
 // coef_bytes: size of one complex matrix entry (16 for binary64 and
 // float-float, 8 for binary32), for exchanging entries when an op's target
 // is flipped.
-void plan_register_layout(DevPass* dp, std::vector<DevOp>* ops, int coef_bytes);
+// reorder: let commuting ops whose targets are placed run before ops that
+// need a layout change.
+void plan_register_layout(DevPass* dp, std::vector<DevOp>* ops, int coef_bytes, bool reorder = true);
 
 // Kernel launchers (qt_kernels.cu).  Return a cudaError_t as int.
 // err: device int set to 1 when a bounded wait of the TMA-staged kernel

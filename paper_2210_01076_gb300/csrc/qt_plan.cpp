@@ -460,7 +460,7 @@ void close_all(Bitset* W, const std::vector<Pass>& passes, const std::vector<Bit
 //  - every other op is resolved against the current layout: targets and
 //    conditions become physical bits, a flipped target exchanges the op's
 //    matrix entries (X U X), a flipped condition is marked in the value mask.
-void plan_register_layout(DevPass* dp, std::vector<DevOp>* ops_io, int coef_bytes) {
+void plan_register_layout(DevPass* dp, std::vector<DevOp>* ops_io, int coef_bytes, bool reorder) {
     const int tb = dp->lt + dp->nh;
     dp->reg_kernel = 0;
     if (tb < 7) return;
@@ -482,11 +482,13 @@ void plan_register_layout(DevPass* dp, std::vector<DevOp>* ops_io, int coef_byte
         }
     };
     auto pc = [](uint32_t x) { return __builtin_popcount(x); };
-    // register set of a new layout for ops[i..]: their targets above the lanes
+    std::vector<char> done(ops.size(), 0);
+    // register set of a new layout for op i and the ops not yet placed after
+    // it: their targets above the lanes
     auto choose = [&](size_t i, uint32_t keep) -> uint32_t {
-        uint32_t s = 0;
-        for (size_t j = i; j < ops.size(); ++j) {
-            if (relabel(ops[j])) continue;
+        uint32_t s = targets(ops[i]) & upper;
+        for (size_t j = 0; j < ops.size(); ++j) {
+            if (j == i || done[j] || relabel(ops[j])) continue;
             const uint32_t t = s | (targets(ops[j]) & upper);
             if (pc(t) > nreg) break;
             s = t;
@@ -542,9 +544,46 @@ void plan_register_layout(DevPass* dp, std::vector<DevOp>* ops_io, int coef_byte
         std::memcpy(m + i * coef_bytes, m + j * coef_bytes, size_t(coef_bytes));
         std::memcpy(m + j * coef_bytes, t, size_t(coef_bytes));
     };
+    // Ops that commute (no common tile bit, or both diagonal) may run in any
+    // order.  The ops are taken in list order, except that when the next op
+    // would need a layout change, a later ready op whose targets are already
+    // placed goes first (option `reorder`, on by default).
+    const size_t n = ops.size();
+    std::vector<uint32_t> qm(n);
+    std::vector<char> dg(n);
+    for (size_t i = 0; i < n; ++i) {
+        // every tile bit the op reads or changes (a DIAG outside the tile is a
+        // factor per tile and touches none)
+        qm[i] = targets(ops[i]) | ops[i].cm_tile;
+        if (ops[i].kind == OP_DIAG && ops[i].b0 >= 0) qm[i] |= 1u << ops[i].b0;
+        dg[i] = ops[i].kind == OP_DIAG || ops[i].kind == OP_PHASE;
+    }
+    auto commute = [&](size_t i, size_t j) { return (qm[i] & qm[j]) == 0 || (dg[i] && dg[j]); };
+    std::vector<int> npred(n, 0);
+    for (size_t j = 0; j < n; ++j)
+        for (size_t i = 0; i < j; ++i)
+            if (!commute(i, j)) ++npred[j];
+    auto ready_without_perm = [&](const DevOp& c) {
+        if (relabel(c)) return true;
+        const bool mixed = c.kind == OP_SWAP && (((L.flip >> c.b0) ^ (L.flip >> c.b1)) & 1u);
+        return placed(targets(c)) && !mixed;
+    };
     std::vector<DevOp> out;
     out.reserve(ops.size() + 4);
-    for (size_t i = 0; i < ops.size(); ++i) {
+    for (size_t step = 0; step < n; ++step) {
+        size_t i = n, first = n;
+        for (size_t k = 0; k < n; ++k) {
+            if (done[k] || npred[k] != 0) continue;
+            if (first == n) first = k;
+            if (!reorder || ready_without_perm(ops[k])) {
+                i = k;
+                break;
+            }
+        }
+        if (i == n) i = first;
+        done[i] = 1;
+        for (size_t j = i + 1; j < n; ++j)
+            if (!done[j] && !commute(i, j)) --npred[j];
         DevOp o = ops[i];
         if (relabel(o)) {
             if (o.kind == OP_X) {
