@@ -1,0 +1,298 @@
+// Host check of the register-kernel layout planner (plan_register_layout).
+//
+// For random circuits, every fused pass is planned twice over the same
+// tile-local ops:
+//   reference  the encoded ops applied in list order to a logical tile
+//              (targets and conditions as tile-index bits, global
+//              conditions read from a random tile base);
+//   planned    the planner's output -- dispatch codes on physical lane,
+//              register and warp bits, register renames, layout changes,
+//              relabels with their flip mask -- executed with the register
+//              kernel's semantics on a physical tile, then stored through the
+//              final layout.
+// Both use exact binary64 complex arithmetic on random tile contents; the
+// results must agree to rounding.  This pins the planner's bookkeeping on the
+// CPU; the GPU parity tests pin the kernels against the oracle.
+//
+// Build: g++ -O1 -std=c++17 -I<include> -I<csrc> -I<cuda include>
+//        planner_emulator.cpp -L<pkg> -lqtask
+// Prints "OK <passes> <ops>" and exits 0, or prints the first mismatch and
+// exits 1.
+#include <cmath>
+#include <complex>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <random>
+#include <vector>
+
+#include "qt_internal.h"
+
+using namespace qt;
+using cd = std::complex<double>;
+
+static cd entry(const DevOp& o, int k) { return cd(o.m.d[2 * k], o.m.d[2 * k + 1]); }
+
+// ---------------------------------------------------------------- reference
+static void apply_reference(const DevOp& o, std::vector<cd>& T, int tb, uint64_t base) {
+    if ((base & o.cm_glob) != o.cm_glob) return;
+    const uint32_t n = 1u << tb;
+    auto cond = [&](uint32_t j) { return (j & o.cm_tile) == o.cm_tile; };
+    switch (o.kind) {
+        case OP_DENSE: case OP_REAL: case OP_IREAL: case OP_X: case OP_ANTI: {
+            const uint32_t tbit = 1u << o.b0;
+            for (uint32_t j = 0; j < n; ++j) {
+                if ((j & tbit) || !cond(j)) continue;
+                const cd a = T[j], b = T[j | tbit];
+                if (o.kind == OP_X) {
+                    T[j] = b;
+                    T[j | tbit] = a;
+                } else if (o.kind == OP_ANTI) {
+                    T[j] = entry(o, 0) * b;
+                    T[j | tbit] = entry(o, 1) * a;
+                } else {
+                    T[j] = entry(o, 0) * a + entry(o, 1) * b;
+                    T[j | tbit] = entry(o, 2) * a + entry(o, 3) * b;
+                }
+            }
+            break;
+        }
+        case OP_SWAP: {
+            const uint32_t m0 = 1u << o.b0, m1 = 1u << o.b1;
+            for (uint32_t j = 0; j < n; ++j)
+                if ((j & m0) && !(j & m1) && cond(j)) std::swap(T[j], T[j ^ (m0 | m1)]);
+            break;
+        }
+        case OP_DIAG: {
+            for (uint32_t j = 0; j < n; ++j) {
+                if (!cond(j)) continue;
+                const int bit = o.b0 < 0 ? int((base >> o.gq) & 1u) : int((j >> o.b0) & 1u);
+                T[j] *= entry(o, bit);
+            }
+            break;
+        }
+        case OP_PHASE: {
+            cd f = entry(o, 0);
+            if (o.sub == PH_NEG) f = -1.0;
+            else if (o.sub == PH_POS_I) f = cd(0.0, 1.0);
+            else if (o.sub == PH_NEG_I) f = cd(0.0, -1.0);
+            for (uint32_t j = 0; j < n; ++j)
+                if (cond(j)) T[j] *= f;
+            break;
+        }
+        default:
+            break;
+    }
+}
+
+// ----------------------------------------------------------------- planned
+struct Phys {
+    int nreg, nwarp, R, W;
+    std::vector<cd> v;  // slot (lane, r, w) -> lane + 32 * (r + R * w)
+    cd& at(int lane, int r, int w) { return v[size_t(lane) + 32u * size_t(r + R * w)]; }
+};
+
+static uint32_t layout_index(const int8_t* lane, const int8_t* reg, const int8_t* warp, int nreg, int nwarp,
+                             uint32_t flip, int l, int r, int w) {
+    uint32_t j = 0;
+    for (int i = 0; i < 5; ++i)
+        if ((l >> i) & 1) j |= 1u << (lane ? lane[i] : i);
+    for (int k = 0; k < nreg; ++k)
+        if ((r >> k) & 1) j |= 1u << reg[k];
+    for (int k = 0; k < nwarp; ++k)
+        if ((w >> k) & 1) j |= 1u << warp[k];
+    return j ^ flip;
+}
+
+static void run_planned(const std::vector<DevOp>& ops, const DevPass& dp, std::vector<cd>& T, uint64_t base) {
+    Phys P{dp.nreg, dp.nwarp, 1 << dp.nreg, 1 << dp.nwarp, {}};
+    P.v.assign(size_t(32) * P.R * P.W, 0.0);
+    int8_t reg0[8], warp0[8];
+    for (int k = 0; k < dp.nreg; ++k) reg0[k] = int8_t(dp.layout[k]);
+    for (int w = 0; w < dp.nwarp; ++w) warp0[w] = int8_t(dp.layout[dp.nreg + w]);
+    for (int w = 0; w < P.W; ++w)
+        for (int r = 0; r < P.R; ++r)
+            for (int l = 0; l < 32; ++l) P.at(l, r, w) = T[layout_index(nullptr, reg0, warp0, P.nreg, P.nwarp, 0, l, r, w)];
+    for (const DevOp& o : ops) {
+        const RegHdr& h = o.rh;
+        if (h.code == RC_PERM) {
+            TileLayout from;
+            std::memcpy(&from, &o.m, sizeof from);
+            std::vector<cd> L(T.size());
+            for (int w = 0; w < P.W; ++w)
+                for (int r = 0; r < P.R; ++r)
+                    for (int l = 0; l < 32; ++l)
+                        L[layout_index(from.lane, from.reg, from.warp, P.nreg, P.nwarp, from.flip, l, r, w)] = P.at(l, r, w);
+            for (int w = 0; w < P.W; ++w)
+                for (int r = 0; r < P.R; ++r)
+                    for (int l = 0; l < 32; ++l)
+                        P.at(l, r, w) = L[layout_index(nullptr, o.perm, o.perm + P.nreg, P.nreg, P.nwarp, 0, l, r, w)];
+            continue;
+        }
+        if (h.ren > 0) {
+            const int K = h.ren;
+            for (int w = 0; w < P.W; ++w)
+                for (int l = 0; l < 32; ++l)
+                    for (int r = 0; r < P.R; ++r)
+                        if ((r & 1) && !((r >> K) & 1)) std::swap(P.at(l, r, w), P.at(l, r ^ (1 | (1 << K)), w));
+        }
+        if ((base & o.cm_glob) != o.cm_glob) continue;
+        const uint32_t cmr = h.cm_reg, cvr = h.cv_reg;
+        auto rcond = [&](int r) { return ((uint32_t(r) ^ cvr) & cmr) == cmr; };
+        Phys Q = P;  // values before the op (partners read from here)
+        for (int w = 0; w < P.W; ++w) {
+            for (int l = 0; l < 32; ++l) {
+                const uint32_t ptid = uint32_t(l) | (uint32_t(w) << 5);
+                const bool thr_ok = ((ptid ^ h.cv_thr) & h.cm_thr) == h.cm_thr;
+                const int code = h.code;
+                if (code == RC_DENSE_R || code == RC_REAL_R || code == RC_IREAL_R) {
+                    for (int r = 0; r < P.R; r += 2) {
+                        const cd a = Q.at(l, r, w), b = Q.at(l, r + 1, w);
+                        P.at(l, r, w) = entry(o, 0) * a + entry(o, 1) * b;
+                        P.at(l, r + 1, w) = entry(o, 2) * a + entry(o, 3) * b;
+                    }
+                } else if (code == RC_DENSE_L || code == RC_REAL_L || code == RC_IREAL_L) {
+                    const int hi = (l >> h.a) & 1, pl = l ^ (1 << h.a);
+                    for (int r = 0; r < P.R; ++r) {
+                        const cd own = Q.at(l, r, w), par = Q.at(pl, r, w);
+                        P.at(l, r, w) = hi ? entry(o, 3) * own + entry(o, 2) * par : entry(o, 0) * own + entry(o, 1) * par;
+                    }
+                } else if (code == RC_ANTI_R) {
+                    for (int r = 0; r < P.R; r += 2) {
+                        const cd a = Q.at(l, r, w), b = Q.at(l, r + 1, w);
+                        P.at(l, r, w) = entry(o, 0) * b;
+                        P.at(l, r + 1, w) = entry(o, 1) * a;
+                    }
+                } else if (code == RC_ANTI_L) {
+                    const int hi = (l >> h.a) & 1, pl = l ^ (1 << h.a);
+                    for (int r = 0; r < P.R; ++r) P.at(l, r, w) = entry(o, hi) * Q.at(pl, r, w);
+                } else if (code == RC_X_R) {
+                    for (int r = 0; r < P.R; r += 2)
+                        if (thr_ok && rcond(r)) std::swap(P.at(l, r, w), P.at(l, r + 1, w));
+                } else if (code == RC_X_L) {
+                    const int pl = l ^ (1 << h.a);
+                    for (int r = 0; r < P.R; ++r)
+                        if (thr_ok && rcond(r)) P.at(l, r, w) = Q.at(pl, r, w);
+                } else if (code == RC_SWAP_RR) {
+                    const int K0 = h.a, K1 = h.b;
+                    for (int r = 0; r < P.R; ++r)
+                        if (((r >> K0) & 1) && !((r >> K1) & 1) && thr_ok && rcond(r))
+                            std::swap(P.at(l, r, w), P.at(l, r ^ ((1 << K0) | (1 << K1)), w));
+                } else if (code == RC_SWAP_LR) {
+                    const int b = h.a, K = h.b, pl = l ^ (1 << b);
+                    const bool lb = (l >> b) & 1;
+                    for (int r = 0; r < P.R; ++r) {
+                        if (r & (1 << K)) continue;
+                        const int r1 = r | (1 << K);
+                        if (!(thr_ok && rcond(r))) continue;
+                        if (lb) P.at(l, r, w) = Q.at(pl, r1, w);
+                        else P.at(l, r1, w) = Q.at(pl, r, w);
+                    }
+                } else if (code == RC_SWAP_LL) {
+                    const int mask = (1 << h.a) | (1 << h.b), pl = l ^ mask;
+                    const bool differ = ((l >> h.a) ^ (l >> h.b)) & 1;
+                    for (int r = 0; r < P.R; ++r)
+                        if (differ && thr_ok && rcond(r)) P.at(l, r, w) = Q.at(pl, r, w);
+                } else if (code == RC_DIAG_G || code == RC_DIAG_T) {
+                    const int bit = code == RC_DIAG_G ? int((base >> h.a) & 1u) : int((ptid >> h.a) & 1u);
+                    for (int r = 0; r < P.R; ++r) P.at(l, r, w) *= entry(o, bit);
+                } else if (code == RC_DIAG_R) {
+                    for (int r = 0; r < P.R; ++r) P.at(l, r, w) *= entry(o, (r >> h.a) & 1);
+                } else if (code >= RC_PH_NEG && code <= RC_PH_GEN) {
+                    if (!thr_ok) continue;
+                    cd f = entry(o, 0);
+                    if (code == RC_PH_NEG) f = -1.0;
+                    else if (code == RC_PH_POS_I) f = cd(0.0, 1.0);
+                    else if (code == RC_PH_NEG_I) f = cd(0.0, -1.0);
+                    for (int r = 0; r < P.R; ++r) {
+                        const bool q = h.mcls == 0 ? true : h.mcls == 1 ? bool((r >> h.a) & 1) : rcond(r);
+                        if (q) P.at(l, r, w) *= f;
+                    }
+                }
+            }
+        }
+    }
+    for (int w = 0; w < P.W; ++w)
+        for (int r = 0; r < P.R; ++r)
+            for (int l = 0; l < 32; ++l)
+                T[layout_index(dp.fin.lane, dp.fin.reg, dp.fin.warp, P.nreg, P.nwarp, dp.fin.flip, l, r, w)] = P.at(l, r, w);
+}
+
+int main(int argc, char** argv) {
+    const int ncirc = argc > 1 ? atoi(argv[1]) : 40;
+    std::mt19937_64 rng(20251204);
+    std::uniform_real_distribution<double> U(-1.0, 1.0), ang(0.0, 6.283185307179586);
+    long npasses = 0, nops = 0;
+    for (int ci = 0; ci < ncirc; ++ci) {
+        const int n = 11 + ci % 4;
+        const int th = 3 + ci % 3;
+        qt_circuit* c = nullptr;
+        if (qt_create(n, QT_C128, n, &c) != QT_OK) return 2;
+        qt_set_option(c, "tile_high", th);
+        qt_set_option(c, "merge", ci % 2);
+        const int ngates = 120 + 20 * (ci % 5);
+        for (int gi = 0; gi < ngates; ++gi) {
+            qt_insert_level(c, gi);
+            qt_gate g{};
+            // weight permutations and phases: they exercise relabels and conditions
+            static const int pool[] = {QT_H, QT_X, QT_X, QT_Y, QT_Z, QT_S, QT_SDG, QT_T, QT_RX, QT_RX, QT_RY, QT_RZ,
+                                       QT_U3, QT_CNOT, QT_CNOT, QT_CZ, QT_SWAP, QT_SWAP, QT_CCX, QT_CP};
+            g.kind = pool[rng() % (sizeof pool / sizeof pool[0])];
+            const int nt = g.kind == QT_SWAP ? 2 : 1;
+            const int nc = g.kind == QT_CCX ? 2 : (g.kind == QT_CNOT || g.kind == QT_CZ || g.kind == QT_CP) ? 1 : 0;
+            int q[3];
+            for (int k = 0; k < nt + nc; ++k) {
+                bool fresh;
+                do {
+                    q[k] = int(rng() % uint64_t(n));
+                    fresh = true;
+                    for (int m = 0; m < k; ++m) fresh = fresh && q[m] != q[k];
+                } while (!fresh);
+            }
+            g.ntarget = nt;
+            g.ncontrol = nc;
+            for (int k = 0; k < nt; ++k) g.target[k] = q[k];
+            for (int k = 0; k < nc; ++k) g.control[k] = q[nt + k];
+            for (int k = 0; k < 3; ++k) g.theta[k] = ang(rng);
+            qt_gate_id id;
+            if (qt_insert_gate(c, gi, &g, &id) != QT_OK) return 3;
+        }
+        std::vector<Pass> passes;
+        int dtype = 0, nn = 0;
+        circuit_plan_whole(c, &passes, &dtype, &nn);
+        for (const Pass& ps : passes) {
+            std::vector<DevOp> ops;
+            for (const HostOp& ho : ps.ops) ops.push_back(encode_device_op(dtype, ps, ho));
+            const int tb = ps.lt + ps.nh;
+            if (tb < 7) continue;  // the shared-memory kernel: no register layout
+            for (int reorder = 0; reorder < 2; ++reorder) {
+                DevPass dp;
+                std::memset(&dp, 0, sizeof dp);
+                dp.lt = ps.lt;
+                dp.nh = ps.nh;
+                std::vector<DevOp> planned = ops;
+                plan_register_layout(&dp, &planned, 16, reorder != 0);
+                for (int trial = 0; trial < 2; ++trial) {
+                    const uint64_t base = rng();
+                    std::vector<cd> T(size_t(1) << tb);
+                    for (cd& v : T) v = cd(U(rng), U(rng));
+                    std::vector<cd> ref = T, got = T;
+                    for (const DevOp& o : ops) apply_reference(o, ref, tb, base);
+                    run_planned(planned, dp, got, base);
+                    double err = 0.0;
+                    for (size_t j = 0; j < T.size(); ++j) err = std::max(err, std::abs(ref[j] - got[j]));
+                    if (!(err <= 1e-12)) {
+                        std::printf("MISMATCH circuit %d pass of %zu ops tb %d reorder %d: max err %.3e\n", ci,
+                                    ops.size(), tb, reorder, err);
+                        return 1;
+                    }
+                }
+                nops += long(planned.size());
+            }
+            ++npasses;
+        }
+        qt_destroy(c);
+    }
+    std::printf("OK %ld %ld\n", npasses, nops);
+    return 0;
+}
