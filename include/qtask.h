@@ -168,6 +168,21 @@ qt_status qt_read_amplitudes(const qt_circuit* c, uint64_t first, uint64_t count
 /* Same, into a device buffer of the caller (same element format). */
 qt_status qt_read_amplitudes_device(const qt_circuit* c, uint64_t first, uint64_t count, void* device_dst);
 
+/* Start the same copy to host memory without waiting for it: the amplitudes
+ * are converted into a device snapshot buffer on the circuit's stream (the
+ * library allocates it: count x 16 bytes, 8 for QT_C64, kept until
+ * qt_release_device or qt_destroy), then copied to host_dst on a second
+ * stream, so that edits and the next qt_update_state run while the copy is in
+ * flight.  host_dst (best pinned) must stay valid and untouched until
+ * qt_read_wait returns; a second call first lets the previous copy finish
+ * with the snapshot buffer.  Errors as qt_read_amplitudes, plus QT_ERR_OOM
+ * if the snapshot buffer cannot be allocated. */
+qt_status qt_read_amplitudes_async(qt_circuit* c, uint64_t first, uint64_t count, void* host_dst);
+
+/* Block until the copy started by the last qt_read_amplitudes_async has
+ * arrived in host memory (QT_OK at once if none is in flight). */
+qt_status qt_read_wait(qt_circuit* c);
+
 /* sum_b |alpha_b|^2 of the current state (Section II-A), reduced with
  * FP64-class accuracy for every dtype (float-float partial sums, FP64 tree). */
 qt_status qt_norm(const qt_circuit* c, double* out);

@@ -45,7 +45,7 @@ class qt_update_stats(ctypes.Structure):
 
 EXPORTED = ["qt_create", "qt_destroy", "qt_num_levels", "qt_num_gates", "qt_insert_level", "qt_remove_level",
             "qt_insert_gate", "qt_remove_gate", "qt_replace_gate", "qt_update_state", "qt_read_amplitudes",
-            "qt_read_amplitudes_device", "qt_norm", "qt_norm_static", "qt_fidelity", "qt_probabilities",
+            "qt_read_amplitudes_device", "qt_read_amplitudes_async", "qt_read_wait", "qt_norm", "qt_norm_static", "qt_fidelity", "qt_probabilities",
             "qt_set_option", "qt_set_stream", "qt_num_segments", "qt_segment_info", "qt_last_error",
             "qt_batch_create", "qt_batch_run", "qt_batch_read_amplitudes", "qt_batch_destroy",
             "qt_batch_last_error",
@@ -137,6 +137,8 @@ def load(path: str = LIB_PATH):
         "qt_update_state": [P, i32, ctypes.POINTER(qt_update_stats)],
         "qt_read_amplitudes": [P, u64, u64, P],
         "qt_read_amplitudes_device": [P, u64, u64, P],
+        "qt_read_amplitudes_async": [P, u64, u64, P],
+        "qt_read_wait": [P],
         "qt_norm": [P, ctypes.POINTER(ctypes.c_double)],
         "qt_norm_static": [P, u64, i32, P, P],
         "qt_fidelity": [P, P, ctypes.POINTER(ctypes.c_double)],
@@ -263,6 +265,16 @@ def qt_read_amplitudes(h, first: int, count: int, out: np.ndarray):
 
 def qt_read_amplitudes_device(h, first: int, count: int, device_ptr: int):
     _check(h, load().qt_read_amplitudes_device(h, first, count, ctypes.c_void_p(device_ptr)))
+
+
+def qt_read_amplitudes_async(h, first: int, count: int, out: np.ndarray):
+    assert out.flags.c_contiguous
+    _check(h, load().qt_read_amplitudes_async(h, first, count, out.ctypes.data))
+    return out
+
+
+def qt_read_wait(h):
+    _check(h, load().qt_read_wait(h))
 
 
 def qt_norm(h) -> float:
@@ -393,6 +405,18 @@ class Circuit:
 
     def read_amplitudes_device(self, first: int, count: int, device_ptr: int):
         qt_read_amplitudes_device(self.h, first, count, device_ptr)
+
+    def read_amplitudes_async(self, out: np.ndarray, first: int = 0, count: Optional[int] = None):
+        """Start copying amplitudes into `out` (kept referenced until read_wait)."""
+        if count is None:
+            count = (1 << self.n) - first
+        assert out.size >= count
+        self._async_out = out
+        return qt_read_amplitudes_async(self.h, first, count, out)
+
+    def read_wait(self):
+        qt_read_wait(self.h)
+        self._async_out = None
 
     def norm(self) -> float:
         return qt_norm(self.h)

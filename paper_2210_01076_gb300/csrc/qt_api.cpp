@@ -130,6 +130,13 @@ struct qt_circuit {
     int norm_cap = 0;
     void* d_read = nullptr;
     size_t d_read_cap = 0;
+    // qt_read_amplitudes_async: device snapshot of the converted amplitudes,
+    // copied to the host on copy_stream while the circuit's stream goes on
+    void* d_snap = nullptr;
+    size_t d_snap_cap = 0;
+    cudaStream_t copy_stream = nullptr;
+    cudaEvent_t ev_snap = nullptr, ev_copy = nullptr;
+    bool read_inflight = false;
     int* d_err = nullptr;  // set by a kernel whose bounded wait expired
     int* h_err = nullptr;  // pinned copy read after each update
     cudaEvent_t ev_begin = nullptr, ev_end = nullptr;
@@ -176,6 +183,16 @@ void insert_sorted(Level& L, const Gate& g) {
 void free_device(qt_circuit* c) {
     if (!c->device_ready) return;
     cudaStreamSynchronize(c->stream);
+    if (c->read_inflight) cudaEventSynchronize(c->ev_copy);
+    c->read_inflight = false;
+    cudaFree(c->d_snap);
+    c->d_snap = nullptr;
+    c->d_snap_cap = 0;
+    if (c->copy_stream) cudaStreamDestroy(c->copy_stream);
+    if (c->ev_snap) cudaEventDestroy(c->ev_snap);
+    if (c->ev_copy) cudaEventDestroy(c->ev_copy);
+    c->copy_stream = nullptr;
+    c->ev_snap = c->ev_copy = nullptr;
     for (void* s : c->slabs) cudaFree(s);
     c->slabs.clear();
     cudaFree(c->d_ops);
@@ -896,6 +913,61 @@ qt_status qt_read_amplitudes(const qt_circuit* cc, uint64_t first, uint64_t coun
         }
     }
     if ((e = cudaStreamSynchronize(c->stream)) != cudaSuccess) return cuda_fail(c, e, "read amplitudes");
+    return QT_OK;
+    QT_GUARD_END(c)
+}
+
+qt_status qt_read_amplitudes_async(qt_circuit* c, uint64_t first, uint64_t count, void* host_dst) {
+    if (!c) return QT_ERR_ARG;
+    QT_GUARD_BEGIN
+    if (count && !host_dst) return fail(c, QT_ERR_ARG, "host_dst is NULL");
+    if (first > c->namps() || count > c->namps() - first) return fail(c, QT_ERR_RANGE, "amplitude range");
+    qt_status rs = check_readable(c);
+    if (rs != QT_OK) return rs;
+    cudaError_t e;
+    if (!c->copy_stream) {
+        if ((e = cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking)) != cudaSuccess)
+            return cuda_fail(c, e, "cudaStreamCreate");
+        if ((e = cudaEventCreateWithFlags(&c->ev_snap, cudaEventDisableTiming)) != cudaSuccess ||
+            (e = cudaEventCreateWithFlags(&c->ev_copy, cudaEventDisableTiming)) != cudaSuccess)
+            return cuda_fail(c, e, "cudaEventCreate");
+    }
+    if (count == 0) return QT_OK;
+    const size_t ob = c->dtype == QT_C64 ? 8 : 16;  // output bytes per amplitude
+    const size_t need = size_t(count) * ob;
+    // the snapshot buffer is free once the previous read's copy has finished
+    if (c->read_inflight && (e = cudaStreamWaitEvent(c->stream, c->ev_copy, 0)) != cudaSuccess)
+        return cuda_fail(c, e, "read amplitudes");
+    if (c->d_snap_cap < need) {
+        if ((e = cudaStreamSynchronize(c->stream)) != cudaSuccess) return cuda_fail(c, e, "read amplitudes");
+        cudaFree(c->d_snap);
+        c->d_snap = nullptr;
+        c->d_snap_cap = 0;
+        if ((e = cudaMalloc(&c->d_snap, need)) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(c, QT_ERR_OOM, "snapshot buffer");
+        }
+        c->d_snap_cap = need;
+    }
+    int rc = launch_read_convert(c->dtype, c->d_snap, final_state(c), first, count, c->stream);
+    if (rc) return cuda_fail(c, rc, "read amplitudes");
+    if ((e = cudaEventRecord(c->ev_snap, c->stream)) != cudaSuccess ||
+        (e = cudaStreamWaitEvent(c->copy_stream, c->ev_snap, 0)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(host_dst, c->d_snap, need, cudaMemcpyDeviceToHost, c->copy_stream)) != cudaSuccess ||
+        (e = cudaEventRecord(c->ev_copy, c->copy_stream)) != cudaSuccess)
+        return cuda_fail(c, e, "read amplitudes");
+    c->read_inflight = true;
+    return QT_OK;
+    QT_GUARD_END(c)
+}
+
+qt_status qt_read_wait(qt_circuit* c) {
+    if (!c) return QT_ERR_ARG;
+    QT_GUARD_BEGIN
+    if (!c->read_inflight) return QT_OK;
+    c->read_inflight = false;
+    cudaError_t e = cudaEventSynchronize(c->ev_copy);
+    if (e != cudaSuccess) return cuda_fail(c, e, "read amplitudes");
     return QT_OK;
     QT_GUARD_END(c)
 }
