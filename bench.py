@@ -48,6 +48,26 @@ def rank_info():
     return r, w, lr
 
 
+def rank_seed(rank: int) -> int:
+    """Each rank simulates its own circuit (independent replicas: weak scaling)."""
+    return SEED + 1000 * rank
+
+
+def aggregate_over_ranks(units: float, seconds: float, device=None):
+    """Whole-job (units, seconds) over all ranks: the units every rank
+    processed, summed, and the slowest rank's time, which bounds the job.
+    One rank (or no process group): returned unchanged."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(units), float(seconds)
+    t = torch.tensor([float(seconds)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    a = torch.tensor([float(units)], device=device, dtype=torch.float64)
+    dist.all_reduce(a)
+    return float(a.item()), float(t.item())
+
+
 def measured_peak():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -202,7 +222,7 @@ def run_ours(args):
     dev = torch.device("cuda", local_rank)
     stream = torch.cuda.Stream(device=dev)
 
-    seed = SEED + 1000 * rank  # independent circuits per rank (weak scaling)
+    seed = rank_seed(rank)
     rounds = args.warmup + args.steps
     levels, _, final_model, edits = make_workload(seed, 2 * rounds + 2)
 
@@ -258,16 +278,9 @@ def run_ours(args):
     kern_bytes = sum(s["pass_kernel_bytes"] for s in stats)
     alu_ops = sum(s["pass_kernel_alu_ops"] for s in stats)
     kern_launches = sum(s["pass_kernel_launches"] for s in stats)
-    t_max = elapsed_ms
-    amp_all = amp
-    if world > 1:
-        t = torch.tensor([elapsed_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_max = float(t.item())
-        a = torch.tensor([float(amp)], device=dev, dtype=torch.float64)
-        dist.all_reduce(a)
-        amp_all = float(a.item())
-    value = amp_all / (t_max * 1e-3)
+    amp_all, t_max_s = aggregate_over_ranks(amp, elapsed_ms * 1e-3, dev)
+    t_max = t_max_s * 1e3
+    value = amp_all / t_max_s
 
     # ---- full re-simulation latency on the current circuit (same plan)
     fulls = []
@@ -298,13 +311,8 @@ def run_ours(args):
     c.read_wait()
     barrier()
     te = time.perf_counter() - te0
-    e2e_val = e2e_amp / te if e2e_rounds else None
-    if world > 1:
-        t = torch.tensor([te], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        a = torch.tensor([float(e2e_amp)], device=dev, dtype=torch.float64)
-        dist.all_reduce(a)
-        e2e_val = float(a.item()) / float(t.item()) if e2e_rounds else None
+    e2e_all, te_max = aggregate_over_ranks(e2e_amp, te, dev)
+    e2e_val = e2e_all / te_max if e2e_rounds else None
 
     # ---- accuracy of the final state against the oracle (rank 0; the
     # oracle's state after the same rounds), and the norm
