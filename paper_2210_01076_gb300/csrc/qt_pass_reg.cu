@@ -465,6 +465,10 @@ __global__ void __launch_bounds__(256, reg_min_blocks<A, RB>()) k_pass_reg(typen
         }
     }
     run_ops<A, RB>(x, ops + dp.op_offset, dp.nops, base, lane, wid, tile);
+    // A pass whose gates were all relabels has no ops, so no barrier has
+    // separated the loads from the stores; its final layout sends amplitudes
+    // to positions that other warps of the CTA load (in place: dst == src).
+    if (dp.nops == 0) __syncthreads();
     const TileMap<RB> m = layout_map<RB>(dp.fin, dp.nwarp, lane, wid);
 #pragma unroll
     for (int r = 0; r < R; ++r) {
@@ -692,6 +696,7 @@ __device__ __forceinline__ void batch_tile(typename A::amp_t* __restrict__ state
         }
     }
     run_ops<A, RB>(x, ops + dp.op_offset, dp.nops, base, lane, wid, tile);
+    if (dp.nops == 0) __syncthreads();  // relabels only: the loads of every warp come before any store
     const TileMap<RB> m = layout_map<RB>(dp.fin, dp.nwarp, lane, wid);
 #pragma unroll
     for (int r = 0; r < R; ++r) {

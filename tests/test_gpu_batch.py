@@ -101,3 +101,32 @@ def test_autotuners_pick_a_measured_setting():
         circs.append(cc)
     bt = tuning.tune_batch(circs, tile_high=(3, 5), repeats=1)
     assert bt["best"] is not None and len(bt["table"]) == 2
+
+
+@pytest.mark.parametrize("dtype", ["c128df", "c64"])
+def test_batch_passes_of_relabels_only(dtype):
+    """Circuits closing with a swap network (passes that hold only relabels)
+    in one batched launch, against the oracle."""
+    circs, levels = [], []
+    for k, n in enumerate([12, 13, 14, 15, 16]):
+        rng = np.random.default_rng(k)
+        gates = [W.make_gate("u3", [q], rng.uniform(0, 2 * math.pi, 3)) for q in range(n)]
+        gates += [W.make_gate("cnot", [q + 1, q]) for q in range(n - 1)]
+        for j in range(n - 1, -1, -1):
+            gates.append(W.make_gate("h", [j]))
+            for m in range(j - 1, -1, -1):
+                gates.append(W.make_gate("cp", [j, m], [math.pi / (1 << (j - m))]))
+        gates += [W.make_gate("swap", [i, n - 1 - i]) for i in range(n // 2)]
+        lv = W.asap_levels(n, gates)
+        c = B.Circuit(n, dtype, min(n, 10))
+        c.load_levels(lv)
+        circs.append(c)
+        levels.append(lv)
+    batch = B.Batch(circs)
+    for _ in range(2):
+        batch.run()
+        for k, c in enumerate(circs):
+            assert max_err(batch.read_amplitudes(k), oracle.simulate(c.n, W.flatten(levels[k]))) <= TOL[dtype], k
+    batch.close()
+    for c in circs:
+        c.close()

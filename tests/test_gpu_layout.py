@@ -101,3 +101,29 @@ def test_incremental_edits_on_relabeled_circuits_are_bit_identical(dtype):
         assert np.array_equal(inc, c.read_amplitudes())
     assert max_err(c.read_amplitudes(), oracle.simulate(n, W.flatten(levels))) <= TOL[dtype]
     c.close()
+
+
+def _qft_with_swaps(n):
+    gates = []
+    for j in range(n - 1, -1, -1):
+        gates.append(W.make_gate("h", [j]))
+        for m in range(j - 1, -1, -1):
+            gates.append(W.make_gate("cp", [j, m], [math.pi / (1 << (j - m))]))
+    return gates + [W.make_gate("swap", [i, n - 1 - i]) for i in range(n // 2)]
+
+
+@pytest.mark.parametrize("dtype", DTYPES)
+@pytest.mark.parametrize("n,p", [(16, 10), (22, 14)])
+def test_passes_of_relabels_only(dtype, n, p):
+    """A QFT's closing swap network plans into passes that hold nothing but
+    relabels (no op runs; the final layout alone moves the amplitudes, in
+    place).  Against the oracle, and a re-run gives the same bits."""
+    levels = prep_levels(n, seed=1) + W.asap_levels(n, _qft_with_swaps(n))
+    c, _ = build_circuit(n, levels, dtype, p)
+    c.update_state()
+    a = c.read_amplitudes()
+    assert max_err(a, oracle.simulate(n, W.flatten(levels), nthreads=oracle.max_threads())) <= TOL[dtype]
+    for _ in range(2):
+        c.update_state(force_full=True)
+        assert np.array_equal(a, c.read_amplitudes())
+    c.close()
