@@ -437,19 +437,11 @@ def run_deep30(args):
     L = len(levels)
     inc = []
     for _ in range(args.steps):
-        lvl = int(rng.integers(int(0.9 * L), L))
-        if not ids[lvl]:
+        # every edit changes the plan (a new RZ or CP angle)
+        e = W.tail_edit(rng, levels)
+        if e is None:
             continue
-        k = int(rng.integers(len(ids[lvl])))
-        g = levels[lvl][k]
-        # a one-qubit gate becomes a small RZ, a two-qubit phase a controlled
-        # phase of a nearby angle (CZ = CP(pi)): every edit changes the plan
-        delta = float(rng.normal(0.0, 0.1))
-        if len(g.qubits) == 1:
-            ng = W.make_gate("rz", [g.qubits[0]], [delta])
-        else:
-            theta = g.params[0] if g.name == "cp" else np.pi
-            ng = W.make_gate("cp", list(g.targets) + list(g.controls), [theta + delta])
+        lvl, k, ng = e
         ids[lvl][k] = c.replace_gate(lvl, ids[lvl][k], ng)
         levels[lvl][k] = ng
         inc.append(c.update_state())
@@ -579,15 +571,53 @@ def run_serve(args):
     at_70 = open_loop(0.7 * cap, args.serve_seconds)
     info = srv.info()
     srv.close()
+    accuracy = serve_accuracy(B, circs, mirrors, ns, args.serve_check)
     line = {"metric": "served requests", "workload": "serve64", "dtype": "c64 (fp32)",
             "config": {"circuits": ncirc, "qubits": "16-28", "gates": "300-1500", "edits_per_request": "1-5",
                        "workers": args.serve_workers, "hbm_budget_gb": args.serve_budget_gb},
             "warmup_full_sims_s": warm_s, "capacity_req_s": cap, "at_offered_2000": at_2k,
             "at_70pct_capacity": at_70, "evictions": info["evictions"],
-            "resident_gb": info["resident_bytes"] / 1e9}
+            "resident_gb": info["resident_bytes"] / 1e9, "accuracy_vs_plain_c128": accuracy}
     print(json.dumps(line), flush=True)
     for c in circs:
         c.close()
+
+
+def serve_accuracy(B, circs, mirrors, ns, count):
+    """Accuracy of served results: for `count` of the circuits (the smallest,
+    the largest, the rest drawn by seed) the served complex64 state after
+    all requests against the plain unbatched complex128 (binary64) path run
+    on the same edited circuit -- max-abs amplitude error and fidelity."""
+    order = sorted(range(len(circs)), key=lambda c: ns[c])
+    pick = [order[0], order[-1]]
+    rest = [c for c in order[1:-1]]
+    rng = np.random.default_rng(56)
+    pick += [int(c) for c in rng.choice(rest, size=min(max(count - 2, 0), len(rest)), replace=False)]
+    pick = pick[:count]
+    for c, circ in enumerate(circs):
+        if c not in pick:
+            circ.release_device()
+    worst_err, worst_fid, per = 0.0, 1.0, []
+    for c in pick:
+        circ = circs[c]
+        circ.update_state()  # re-simulates a circuit the server evicted (the same bits)
+        ref = B.Circuit(ns[c], "c128", min(ns[c], 16))
+        ref.set_option("ckpt_interval", len(mirrors[c]) + 1)  # no checkpoints needed
+        ref.load_levels(mirrors[c])
+        ref.update_state()
+        fid = circ.fidelity(ref)
+        err, chunk = 0.0, 1 << 22
+        for first in range(0, 1 << ns[c], chunk):
+            cnt = min(chunk, (1 << ns[c]) - first)
+            a = circ.read_amplitudes(first, cnt).astype(np.complex128)
+            err = max(err, float(np.max(np.abs(a - ref.read_amplitudes(first, cnt)))))
+        ref.close()
+        circ.release_device()
+        per.append({"qubits": ns[c], "gates": int(sum(len(lv) for lv in mirrors[c])), "max_abs_err": err,
+                    "fidelity": fid})
+        worst_err, worst_fid = max(worst_err, err), min(worst_fid, fid)
+    return {"circuits_checked": len(per), "max_abs_err": worst_err, "min_fidelity": worst_fid,
+            "tolerance": {"max_abs": 1e-5, "fidelity": 1 - 1e-6}, "per_circuit": per}
 
 
 def run_batch(args):
@@ -603,19 +633,7 @@ def run_batch(args):
     B.load()
     rng = np.random.default_rng(404)
     circs, levels, ids = [], [], []
-    for k in range(args.batch_circuits):
-        n = int(rng.integers(10, 21))
-        depth = int(rng.integers(50, 401))
-        gates, last = [], [-1] * n
-        while True:
-            g = W.random_gate(rng, n, 0.4)
-            lv = 1 + max(last[q] for q in g.qubits)
-            if lv >= depth:
-                break
-            for q in g.qubits:
-                last[q] = lv
-            gates.append(g)
-        lvls = W.asap_levels(n, gates)
+    for n, lvls in W.batch_circuits(args.batch_circuits, rng):
         c = B.Circuit(n, "c64", min(n, 16))
         ids.append(c.load_levels(lvls))
         levels.append([list(x) for x in lvls])
@@ -626,12 +644,10 @@ def run_batch(args):
     rounds = []
     for _ in range(args.batch_rounds):
         for k, c in enumerate(circs):
-            cand = [(l, j) for l, lv in enumerate(levels[k]) for j, g in enumerate(lv) if g.name in ("rz", "ry")]
-            if not cand:
+            e = W.rotation_edit(rng, levels[k])
+            if e is None:
                 continue
-            l, j = cand[int(rng.integers(len(cand)))]
-            g = levels[k][l][j]
-            ng = g._replace(params=(g.params[0] + float(rng.normal(0.0, 0.1)),))
+            l, j, ng = e
             ids[k][l][j] = c.replace_gate(l, ids[k][l][j], ng)
             levels[k][l][j] = ng
         rounds.append(batch.run())
@@ -715,6 +731,8 @@ def main():
     ap.add_argument("--serve-budget-gb", type=float, default=150.0)
     ap.add_argument("--serve-seconds", type=float, default=2.0)
     ap.add_argument("--serve-burst", type=int, default=200)
+    ap.add_argument("--serve-check", type=int, default=6,
+                    help="served circuits checked against the plain complex128 path afterwards")
     ap.add_argument("--dtype", default="c128df", choices=["c128df", "c64", "c128"], help="deep30 only")
     ap.add_argument("--deep-ckpt", type=int, default=48, help="deep30: levels per checkpoint segment")
     args = ap.parse_args()

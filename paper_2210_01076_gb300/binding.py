@@ -421,6 +421,13 @@ class Circuit:
     def norm(self) -> float:
         return qt_norm(self.h)
 
+    def release_device(self):
+        """Free the device state and checkpoints; the next update re-simulates."""
+        qt_release_device(self.h)
+
+    def device_bytes(self) -> int:
+        return qt_device_bytes(self.h)
+
     def fidelity(self, other: "Circuit") -> float:
         return qt_fidelity(self.h, other.h)
 

@@ -99,6 +99,49 @@ def random_circuit(n: int, ngates: int, seed: int, p_multi: Optional[float] = No
     return asap_levels(n, [random_gate(rng, n, p_multi) for _ in range(ngates)])
 
 
+def batch_circuits(count: int, rng: np.random.Generator, p_multi: float = 0.4) -> List[Tuple[int, List[List[Gate]]]]:
+    """The batched-synthesis shape: `count` circuits, qubit counts uniform in
+    [10, 20], ASAP depths uniform in [50, 400]; gates are drawn until the
+    next one would reach the drawn depth.  Returns (n, levels) pairs."""
+    out = []
+    for _ in range(count):
+        n = int(rng.integers(10, 21))
+        depth = int(rng.integers(50, 401))
+        gates, last = [], [-1] * n
+        while True:
+            g = random_gate(rng, n, p_multi)
+            lv = 1 + max(last[q] for q in g.qubits)
+            if lv >= depth:
+                break
+            for q in g.qubits:
+                last[q] = lv
+            gates.append(g)
+        out.append((n, asap_levels(n, gates)))
+    return out
+
+
+_INVERSE_NAME = {"s": "sdg", "sdg": "s", "t": "tdg", "tdg": "t"}
+
+
+def inverse_gate(g: Gate) -> Gate:
+    """The gate's inverse under the rotation conventions of the gate table:
+    rotations and CP negate their angle, U3(theta, phi, lam) becomes
+    U3(-theta, -lam, -phi), S/T become their daggers, the rest are
+    self-inverse."""
+    if g.name in ("rx", "ry", "rz", "cp"):
+        return g._replace(params=(-g.params[0],))
+    if g.name == "u3":
+        th, ph, la = g.params
+        return g._replace(params=(-th, -la, -ph))
+    return g._replace(name=_INVERSE_NAME.get(g.name, g.name))
+
+
+def inverse_levels(levels: List[List[Gate]]) -> List[List[Gate]]:
+    """Levels of the inverse circuit: levels in reverse order, each gate
+    inverted (gates within a level act on disjoint qubits and commute)."""
+    return [[inverse_gate(g) for g in lv] for lv in reversed(levels)]
+
+
 def qft_like_circuit(n: int, ngates: int, seed: int) -> List[List[Gate]]:
     """QFT-style H + controlled-phase ladders interleaved with random U3/CZ layers."""
     rng = np.random.default_rng(seed)
@@ -225,6 +268,36 @@ def edit_stream(model: CircuitModel, rounds: int, seed: int, p_multi: Optional[f
     for _ in range(rounds):
         k = int(rng.integers(min_edits, max_edits + 1))
         yield edit_round(rng, model, p_multi, k)
+
+
+def rotation_edit(rng: np.random.Generator, levels: List[List[Gate]]):
+    """The batched loop's parameter edit: a uniformly chosen RZ or RY gate
+    has its angle moved by N(0, 0.1).  Returns (level, index, new gate), or
+    None when the circuit has no such gate."""
+    cand = [(l, j) for l, lv in enumerate(levels) for j, g in enumerate(lv) if g.name in ("rz", "ry")]
+    if not cand:
+        return None
+    l, j = cand[int(rng.integers(len(cand)))]
+    g = levels[l][j]
+    return l, j, g._replace(params=(g.params[0] + float(rng.normal(0.0, 0.1)),))
+
+
+def tail_edit(rng: np.random.Generator, levels: List[List[Gate]], tail: float = 0.1):
+    """The deep circuit's single-gate edit in the last `tail` of the levels:
+    a one-qubit gate becomes a small RZ, a two-qubit phase a controlled phase
+    of a nearby angle (CZ counts as CP(pi)).  Returns (level, index, new
+    gate), or None when the drawn level is empty."""
+    L = len(levels)
+    lvl = int(rng.integers(int((1.0 - tail) * L), L))
+    if not levels[lvl]:
+        return None
+    k = int(rng.integers(len(levels[lvl])))
+    g = levels[lvl][k]
+    delta = float(rng.normal(0.0, 0.1))
+    if len(g.qubits) == 1:
+        return lvl, k, make_gate("rz", [g.qubits[0]], [delta])
+    theta = g.params[0] if g.name == "cp" else math.pi
+    return lvl, k, make_gate("cp", list(g.targets) + list(g.controls), [theta + delta])
 
 
 def random_state(n: int, seed: int, dtype=np.complex128) -> np.ndarray:

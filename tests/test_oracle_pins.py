@@ -288,3 +288,37 @@ def test_fig2_circuit_is_uniform_before_and_after_edit(golden_dir):
     for edited in (False, True):
         psi = oracle.simulate(golden["n"], fig2_gates(golden, edited))
         assert np.max(np.abs(psi - 1 / math.sqrt(32))) <= TOL
+
+
+@pytest.mark.parametrize("name", ALL_TEST_KINDS)
+def test_workloads_inverse_gate_is_the_inverse(name):
+    """The input generator's inverse-gate rule (used to build U then U-dagger
+    circuits at full size) against the oracle: the inverse's base matrix is
+    the adjoint of the gate's."""
+    rng = np.random.default_rng(9)
+    for _ in range(4):
+        g = W.random_gate(rng, 5, kinds=[name])
+        gi = W.inverse_gate(g)
+        assert gi.qubits == g.qubits
+        a = oracle.base_matrix(g.name, g.params)
+        b = oracle.base_matrix(gi.name, gi.params)
+        assert np.max(np.abs(b - a.conj().T)) <= TOL
+
+
+def test_inverse_levels_undo_a_random_circuit():
+    n = 8
+    levels = W.random_circuit(n, 300, seed=4, p_multi=0.4)
+    psi = oracle.simulate(n, W.flatten(levels) + W.flatten(W.inverse_levels(levels)))
+    want = np.zeros(1 << n)
+    want[0] = 1.0
+    assert np.max(np.abs(psi - want)) <= 1e-12
+
+
+def test_batch_circuit_shapes():
+    rng = np.random.default_rng(404)
+    circs = W.batch_circuits(40, rng)
+    for n, levels in circs:
+        assert 10 <= n <= 20 and 1 <= len(levels) <= 400
+        for lv in levels:
+            qs = [q for g in lv for q in g.qubits]
+            assert len(qs) == len(set(qs)) and all(0 <= q < n for q in qs)
