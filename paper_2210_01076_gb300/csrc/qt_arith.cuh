@@ -112,6 +112,7 @@ struct ArF64 {
         return {__shfl_xor_sync(0xffffffffu, a.re, mask), __shfl_xor_sync(0xffffffffu, a.im, mask)};
     }
     static __device__ __forceinline__ cx matp(const DevOp* op, int k) { return {op->m.d[2 * k], op->m.d[2 * k + 1]}; }
+    static __device__ __forceinline__ cx coef(const PhTerm& t) { return {t.f.d[0], t.f.d[1]}; }
     static __device__ __forceinline__ cx sel(bool c, cx a, cx b) { return c ? a : b; }
     static __device__ __forceinline__ cx mv(cx a) { return a; }
 };
@@ -152,6 +153,7 @@ struct ArF32 {
         return {__shfl_xor_sync(0xffffffffu, a.re, mask), __shfl_xor_sync(0xffffffffu, a.im, mask)};
     }
     static __device__ __forceinline__ cx matp(const DevOp* op, int k) { return {op->m.f[2 * k], op->m.f[2 * k + 1]}; }
+    static __device__ __forceinline__ cx coef(const PhTerm& t) { return {t.f.f[0], t.f.f[1]}; }
     static __device__ __forceinline__ cx sel(bool c, cx a, cx b) { return c ? a : b; }
     static __device__ __forceinline__ cx mv(cx a) { return {fmul_c(a.re, 1.0f), fmul_c(a.im, 1.0f)}; }
 };
@@ -204,6 +206,7 @@ struct ArDF {
     static __device__ __forceinline__ cx matp(const DevOp* op, int k) {
         return {{op->m.f[4 * k], op->m.f[4 * k + 1]}, {op->m.f[4 * k + 2], op->m.f[4 * k + 3]}};
     }
+    static __device__ __forceinline__ cx coef(const PhTerm& t) { return {{t.f.f[0], t.f.f[1]}, {t.f.f[2], t.f.f[3]}}; }
     static __device__ __forceinline__ cx sel(bool c, cx a, cx b) { return c ? a : b; }
 };
 

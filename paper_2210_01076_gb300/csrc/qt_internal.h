@@ -167,6 +167,7 @@ enum RegCode : uint8_t {
     RC_DIAG_T,   // thread-index bit a (lane bits 0-4, warp bits 5-7): one factor per thread
     RC_DIAG_R,   // register bit a
     RC_PH_NEG, RC_PH_POS_I, RC_PH_NEG_I, RC_PH_GEN,
+    RC_PH_GROUP,  // consecutive phases merged: DevOp::b1 terms (PhTerm) in the slots that follow
     RC_NOP
 };
 
@@ -210,6 +211,29 @@ struct DevOp {
 };
 static_assert(sizeof(DevOp) == 128 && offsetof(DevOp, rh) == 48 && offsetof(DevOp, m) == 64, "DevOp layout");
 
+// One phase of a merged group (RC_PH_GROUP), four to a DevOp slot after the
+// group's header.  A thread multiplies together the factors of a step's
+// terms whose conditions hold for it (outside the tile: the tile base's bits
+// in cm_glob are 1; thread index: (tid ^ cv_thr) & cm_thr == cm_thr), then
+// multiplies the product into its amplitudes of the step's class: all of
+// them (mcls 0) or those whose register index has bit k set (mcls 1).
+struct PhTerm {
+    union {
+        double d[2];
+        float f[4];
+    } f;               // the factor, encoded like entry 0 of DevOp::m
+    uint64_t cm_glob;
+    uint16_t cm_thr, cv_thr;
+    uint8_t last;      // last term of its step
+    uint8_t mcls, k;   // the step's registers
+    uint8_t pad;
+};
+static_assert(sizeof(PhTerm) == 32, "PhTerm layout");
+constexpr int kTermsPerSlot = int(sizeof(DevOp) / sizeof(PhTerm));
+// Ops the register kernel stages in shared memory at a time; a merged
+// group's header and its term slots never straddle two chunks.
+constexpr int kOpChunk = 64;
+
 struct DevPass {
     int32_t p;             // log2 partition size
     int32_t lt;            // tile low bits
@@ -227,6 +251,7 @@ struct DevPass {
     int32_t layout[8];     // tile bit of register bit k (k < nreg), then of warp bit w
     int32_t tma;           // 1: persistent register kernel with bulk-copy (TMA) staging
     int32_t test_stall;    // 1: withhold the staging copies so the bounded wait expires (test hook)
+    int32_t groups;        // 1: the ops hold merged phase groups (RC_PH_GROUP)
     TileLayout fin;        // register kernel: the layout the tile is stored from
 };
 
@@ -237,7 +262,10 @@ struct DevPass {
 // is flipped.
 // reorder: let commuting ops whose targets are placed run before ops that
 // need a layout change.
-void plan_register_layout(DevPass* dp, std::vector<DevOp>* ops, int coef_bytes, bool reorder = true);
+// phase_groups: merge runs of phases into RC_PH_GROUP ops where that is
+// estimated to save work (sets dp->groups).
+void plan_register_layout(DevPass* dp, std::vector<DevOp>* ops, int coef_bytes, bool reorder = true,
+                          bool phase_groups = true);
 
 // Kernel launchers (qt_kernels.cu).  Return a cudaError_t as int.
 // err: device int set to 1 when a bounded wait of the TMA-staged kernel
@@ -246,6 +274,9 @@ int launch_pass(int dtype, void* dst, const void* src, const DevPass& dp, const 
                 const uint32_t* worklist, uint32_t ngroups, int* err, void* stream);
 int launch_pass_reg(int dtype, void* dst, const void* src, const DevPass& dp, const DevOp* ops,
                     const uint32_t* worklist, uint32_t ngroups, int* err, void* stream);
+// The same for passes with merged phase groups (dp.groups; qt_pass_grp.cu).
+int launch_pass_reg_groups(int dtype, void* dst, const void* src, const DevPass& dp, const DevOp* ops,
+                           const uint32_t* worklist, uint32_t ngroups, int* err, void* stream);
 int launch_copy_parts(int dtype, void* dst, const void* src, int p, const uint32_t* parts, uint32_t nparts,
                       void* stream);
 int launch_init_zero_state(int dtype, void* state, uint64_t namps, void* stream);

@@ -27,6 +27,15 @@
 #include "qt_arith.cuh"
 #include "qt_internal.h"
 
+// This file is compiled twice: as itself, with the kernels that have no
+// merged phase groups (RC_PH_GROUP) and the library's entry points, and from
+// qt_pass_grp.cu with QT_PASS_PHASE_GROUPS = 1, the same kernels with group
+// support (a separate instantiation, so that passes without groups run code
+// that has none).
+#ifndef QT_PASS_PHASE_GROUPS
+#define QT_PASS_PHASE_GROUPS 0
+#endif
+
 namespace qt {
 
 template <int V>
@@ -216,6 +225,23 @@ struct RegOps {
         for (int r = 0; r < R; ++r) x[r] = A::mul(A::matp(op, (r >> k) & 1), x[r]);
     }
 
+    // multiply all the thread's amplitudes (mcls 0) or those whose register
+    // index has bit k set (mcls 1) by f
+    template <class F>
+    static __device__ __forceinline__ void apply01(cx (&x)[R], int mcls, int k, F&& f) {
+        if (mcls == 0) {
+#pragma unroll
+            for (int r = 0; r < R; ++r) x[r] = f(x[r]);
+        } else {
+            dispatch_k<RB>(k, [&](auto kc) {
+                constexpr int K = decltype(kc)::value;
+#pragma unroll
+                for (int r = 0; r < R; ++r)
+                    if ((r >> K) & 1) x[r] = f(x[r]);
+            });
+        }
+    }
+
     // multiply the amplitudes whose conditions hold by the phase; with one
     // unflipped register condition bit (mcls 1, bit k) the registers that
     // cannot qualify are skipped at compile time
@@ -334,7 +360,7 @@ __device__ __forceinline__ TileMap<RB> layout_map(const TileLayout& L, int nwarp
 // every op against the layout it runs in; the kernel needs a layout only at
 // OP_PERM, which carries the old one.  `tile` is the shared-memory buffer
 // for layout changes.  Every thread of the CTA must call this.
-template <class A, int RB>
+template <class A, int RB, bool PG>
 __device__ __forceinline__ void run_ops(typename A::cx (&x)[1 << RB], const DevOp* __restrict__ pops, int nops,
                                         uint64_t base, uint32_t lane, uint32_t wid, typename A::amp_t* tile) {
     using RO = RegOps<A, RB>;
@@ -346,7 +372,6 @@ __device__ __forceinline__ void run_ops(typename A::cx (&x)[1 << RB], const DevO
     // dispatch code, bits and conditions, resolved on the host) is one
     // 16-byte load; the dispatch is a short if-chain by op class (measured
     // faster than a jump table, and than loading the next header early).
-    constexpr int kOpChunk = 64;
     __shared__ __align__(16) DevOp s_ops[kOpChunk];
     for (int c0 = 0; c0 < nops; c0 += kOpChunk) {
     const int cn = nops - c0 < kOpChunk ? nops - c0 : kOpChunk;
@@ -413,6 +438,28 @@ __device__ __forceinline__ void run_ops(typename A::cx (&x)[1 << RB], const DevO
         } else if (code <= RC_DIAG_R) {
             if (code == RC_DIAG_R) RO::diag_r(x, op, h.a);
             else RO::diag_u(x, op, code == RC_DIAG_G ? int((base >> h.a) & 1u) : int((threadIdx.x >> h.a) & 1u));
+        } else if (PG && code == RC_PH_GROUP) {
+            if constexpr (PG) {
+                // Merged phases, step by step: a thread multiplies the factors of
+                // the step's terms whose conditions hold for it, then applies the
+                // product to the step's registers.
+                const int nt = op->b1;
+                for (int i = 0; i < nt; ++i) {
+                    cx f = A::matp(op, 0);
+                    bool go = false;
+                    for (;; ++i) {
+                        const PhTerm& t = reinterpret_cast<const PhTerm*>(op + 1)[i];
+                        if ((base & t.cm_glob) == t.cm_glob && ((threadIdx.x ^ t.cv_thr) & t.cm_thr) == t.cm_thr) {
+                            f = go ? A::mul(A::coef(t), f) : A::coef(t);
+                            go = true;
+                        }
+                        if (t.last || i + 1 == nt) break;
+                    }
+                    const PhTerm& tl = reinterpret_cast<const PhTerm*>(op + 1)[i];
+                    if (go) RO::apply01(x, tl.mcls, tl.k, [&](cx v) { return A::mul(f, v); });
+                }
+                oi += (nt + kTermsPerSlot - 1) / kTermsPerSlot;  // the term slots
+            }
         } else if (thr_ok) {
             if (code == RC_PH_NEG) RO::masked(x, h.mcls, h.a, cmr, cvr, [](cx v) { return A::neg(v); });
             else if (code == RC_PH_POS_I) RO::masked(x, h.mcls, h.a, cmr, cvr, [](cx v) { return A::mul_i(v); });
@@ -439,7 +486,7 @@ constexpr int reg_min_blocks() {
             (1 << RB) * int(sizeof(typename A::amp_t)) / 4 <= 32) ? 4 : 1;
 }
 
-template <class A, int RB>
+template <class A, int RB, bool PG>
 __global__ void __launch_bounds__(256, reg_min_blocks<A, RB>()) k_pass_reg(typename A::amp_t* __restrict__ dst,
                                                    const typename A::amp_t* __restrict__ src, const DevPass dp,
                                                    const DevOp* __restrict__ ops,
@@ -464,7 +511,7 @@ __global__ void __launch_bounds__(256, reg_min_blocks<A, RB>()) k_pass_reg(typen
             x[r] = A::ld(src[base | choff[j >> dp.lt] | (j & lowmask)]);
         }
     }
-    run_ops<A, RB>(x, ops + dp.op_offset, dp.nops, base, lane, wid, tile);
+    run_ops<A, RB, PG>(x, ops + dp.op_offset, dp.nops, base, lane, wid, tile);
     // A pass whose gates were all relabels has no ops, so no barrier has
     // separated the loads from the stores; its final layout sends amplitudes
     // to positions that other warps of the CTA load (in place: dst == src).
@@ -533,7 +580,7 @@ __device__ __forceinline__ void bulk_g2s(void* dst_smem, const void* src_gmem, u
         : "memory");
 }
 
-template <class A, int RB>
+template <class A, int RB, bool PG>
 __global__ void __launch_bounds__(256, (RB <= 3 ? 3 : 1)) k_pass_tma(typename A::amp_t* __restrict__ dst,
                                                    const typename A::amp_t* __restrict__ src, const DevPass dp,
                                                    const DevOp* __restrict__ ops,
@@ -586,7 +633,7 @@ __global__ void __launch_bounds__(256, (RB <= 3 ? 3 : 1)) k_pass_tma(typename A:
         }
         __syncthreads();  // inbuf is free: stage the next tile while computing this one
         if (t + gridDim.x < ntiles) issue(t + gridDim.x);
-        run_ops<A, RB>(x, ops + dp.op_offset, dp.nops, base, lane, wid, tile);
+        run_ops<A, RB, PG>(x, ops + dp.op_offset, dp.nops, base, lane, wid, tile);
         const TileMap<RB> m = layout_map<RB>(dp.fin, dp.nwarp, lane, wid);
 #pragma unroll
         for (int r = 0; r < R; ++r) {
@@ -596,7 +643,7 @@ __global__ void __launch_bounds__(256, (RB <= 3 ? 3 : 1)) k_pass_tma(typename A:
     }
 }
 
-template <class A, int RB>
+template <class A, int RB, bool PG>
 int launch_reg_t(void* dst, const void* src, const DevPass& dp, const DevOp* ops, const uint32_t* worklist,
                  uint32_t ngroups, int* err, cudaStream_t st) {
     using amp_t = typename A::amp_t;
@@ -610,11 +657,11 @@ int launch_reg_t(void* dst, const void* src, const DevPass& dp, const DevOp* ops
         static bool attr_set = false;
         if (!attr_set) {
             cudaError_t e =
-                cudaFuncSetAttribute(k_pass_reg<A, RB>, cudaFuncAttributeMaxDynamicSharedMemorySize, 128 * 1024);
+                cudaFuncSetAttribute(k_pass_reg<A, RB, PG>, cudaFuncAttributeMaxDynamicSharedMemorySize, 128 * 1024);
             if (e != cudaSuccess) return int(e);
             attr_set = true;
         }
-        k_pass_reg<A, RB><<<unsigned(nblocks), threads, tile_bytes, st>>>(
+        k_pass_reg<A, RB, PG><<<unsigned(nblocks), threads, tile_bytes, st>>>(
             static_cast<amp_t*>(dst), static_cast<const amp_t*>(src), dp, ops, worklist);
         return int(cudaGetLastError());
     }
@@ -622,7 +669,7 @@ int launch_reg_t(void* dst, const void* src, const DevPass& dp, const DevOp* ops
     static int nsm = 0;
     if (!tattr_set) {
         cudaError_t e =
-            cudaFuncSetAttribute(k_pass_tma<A, RB>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
+            cudaFuncSetAttribute(k_pass_tma<A, RB, PG>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
         if (e != cudaSuccess) return int(e);
         int dev = 0;
         cudaGetDevice(&dev);
@@ -631,27 +678,47 @@ int launch_reg_t(void* dst, const void* src, const DevPass& dp, const DevOp* ops
     }
     const size_t smem = 2 * tile_bytes;
     int per_sm = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pass_tma<A, RB>, int(threads), smem);
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pass_tma<A, RB, PG>, int(threads), smem);
     if (e != cudaSuccess) return int(e);
     if (per_sm < 1) per_sm = 1;
     const uint64_t grid = std::min<uint64_t>(nblocks, uint64_t(nsm) * uint64_t(per_sm));
-    k_pass_tma<A, RB><<<unsigned(grid), threads, smem, st>>>(static_cast<amp_t*>(dst),
+    k_pass_tma<A, RB, PG><<<unsigned(grid), threads, smem, st>>>(static_cast<amp_t*>(dst),
                                                              static_cast<const amp_t*>(src), dp, ops, worklist,
                                                              uint32_t(nblocks), err);
     return int(cudaGetLastError());
 }
 
-template <class A>
+template <class A, bool PG>
 int launch_reg_a(void* dst, const void* src, const DevPass& dp, const DevOp* ops, const uint32_t* worklist,
                  uint32_t ngroups, int* err, cudaStream_t st) {
     switch (dp.nreg) {
-        case 2: return launch_reg_t<A, 2>(dst, src, dp, ops, worklist, ngroups, err, st);
-        case 3: return launch_reg_t<A, 3>(dst, src, dp, ops, worklist, ngroups, err, st);
-        case 4: return launch_reg_t<A, 4>(dst, src, dp, ops, worklist, ngroups, err, st);
-        case 5: return launch_reg_t<A, 5>(dst, src, dp, ops, worklist, ngroups, err, st);
+        case 2: return launch_reg_t<A, 2, PG>(dst, src, dp, ops, worklist, ngroups, err, st);
+        case 3: return launch_reg_t<A, 3, PG>(dst, src, dp, ops, worklist, ngroups, err, st);
+        case 4: return launch_reg_t<A, 4, PG>(dst, src, dp, ops, worklist, ngroups, err, st);
+        case 5: return launch_reg_t<A, 5, PG>(dst, src, dp, ops, worklist, ngroups, err, st);
         default: return int(cudaErrorInvalidConfiguration);
     }
 }
+
+// The register kernels of this translation unit for every dtype.
+template <bool PG>
+int launch_pass_reg_t(int dtype, void* dst, const void* src, const DevPass& dp, const DevOp* ops,
+                      const uint32_t* worklist, uint32_t ngroups, int* err, void* stream) {
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    switch (dtype) {
+        case QT_C128: return launch_reg_a<ArF64, PG>(dst, src, dp, ops, worklist, ngroups, err, st);
+        case QT_C64: return launch_reg_a<ArF32, PG>(dst, src, dp, ops, worklist, ngroups, err, st);
+        case QT_C128_DF: return launch_reg_a<ArDF, PG>(dst, src, dp, ops, worklist, ngroups, err, st);
+        default: return int(cudaErrorInvalidValue);
+    }
+}
+
+#if QT_PASS_PHASE_GROUPS
+int launch_pass_reg_groups(int dtype, void* dst, const void* src, const DevPass& dp, const DevOp* ops,
+                           const uint32_t* worklist, uint32_t ngroups, int* err, void* stream) {
+    return launch_pass_reg_t<true>(dtype, dst, src, dp, ops, worklist, ngroups, err, stream);
+}
+#else
 
 // ------------------------------------------------------------ batched runs --
 // Many independent circuits in one persistent launch.  Tiles are dequeued
@@ -695,7 +762,7 @@ __device__ __forceinline__ void batch_tile(typename A::amp_t* __restrict__ state
             x[r] = A::ld(__ldcg(&state[base | choff[j >> dp.lt] | (j & lowmask)]));  // L2: written by other SMs
         }
     }
-    run_ops<A, RB>(x, ops + dp.op_offset, dp.nops, base, lane, wid, tile);
+    run_ops<A, RB, false>(x, ops + dp.op_offset, dp.nops, base, lane, wid, tile);
     if (dp.nops == 0) __syncthreads();  // relabels only: the loads of every warp come before any store
     const TileMap<RB> m = layout_map<RB>(dp.fin, dp.nwarp, lane, wid);
 #pragma unroll
@@ -824,13 +891,9 @@ int launch_batch(int dtype, void* arena, const BatchPass* passes, int npasses, c
 
 int launch_pass_reg(int dtype, void* dst, const void* src, const DevPass& dp, const DevOp* ops,
                     const uint32_t* worklist, uint32_t ngroups, int* err, void* stream) {
-    cudaStream_t st = static_cast<cudaStream_t>(stream);
-    switch (dtype) {
-        case QT_C128: return launch_reg_a<ArF64>(dst, src, dp, ops, worklist, ngroups, err, st);
-        case QT_C64: return launch_reg_a<ArF32>(dst, src, dp, ops, worklist, ngroups, err, st);
-        case QT_C128_DF: return launch_reg_a<ArDF>(dst, src, dp, ops, worklist, ngroups, err, st);
-        default: return int(cudaErrorInvalidValue);
-    }
+    if (dp.groups) return launch_pass_reg_groups(dtype, dst, src, dp, ops, worklist, ngroups, err, stream);
+    return launch_pass_reg_t<false>(dtype, dst, src, dp, ops, worklist, ngroups, err, stream);
 }
+#endif  // QT_PASS_PHASE_GROUPS
 
 }  // namespace qt

@@ -446,6 +446,130 @@ void close_all(Bitset* W, const std::vector<Pass>& passes, const std::vector<Bit
     }
 }
 
+// ------------------------------------------------ merged phase groups --
+namespace {
+
+bool is_phase_code(uint8_t c) { return c >= RC_PH_NEG && c <= RC_PH_GEN; }
+bool is_diag_code(uint8_t c) { return is_phase_code(c) || (c >= RC_DIAG_G && c <= RC_DIAG_R); }
+
+// A resolved phase op that can be a term of a group: every amplitude of the
+// thread, or those with one (unflipped) register bit set.
+bool groupable(const DevOp& o) { return is_phase_code(o.rh.code) && o.rh.mcls <= 1 && o.rh.ren == 0; }
+
+// Estimated per-thread work in units of one complex multiply: an op's fixed
+// decode cost, then its multiplies (a +-1 / +-i phase is a sign change and a
+// move, not a multiply).
+struct PhaseCost {
+    double op, move;
+    explicit PhaseCost(int coef_bytes)
+        : op(coef_bytes == 8 ? 4.0 : 0.4), move(coef_bytes == 8 ? 0.5 : 0.1) {}
+    double single(const DevOp& o, int R) const {
+        const double regs = o.rh.mcls == 0 ? R : o.rh.mcls == 1 ? R / 2.0 : R / 4.0;
+        return op + regs * (o.rh.code == RC_PH_GEN ? 1.0 : move);
+    }
+    double group(int nterms, int nsteps, double regs) const { return op * (1 + 0.5 * nsteps) + 1.25 * nterms + regs; }
+};
+
+// Emit the merged group of the terms in `m` (all groupable): one step for the
+// terms on every register of the thread, one per register bit.
+void emit_group(std::vector<DevOp>* out, const std::vector<const DevOp*>& m, int coef_bytes, int nreg) {
+    std::vector<PhTerm> terms;
+    for (int cls = -1; cls < nreg; ++cls) {
+        const size_t first = terms.size();
+        for (const DevOp* o : m) {
+            const int oc = o->rh.mcls == 0 ? -1 : o->rh.a;
+            if (oc != cls) continue;
+            PhTerm t;
+            std::memset(&t, 0, sizeof t);
+            std::memcpy(&t.f, &o->m, size_t(coef_bytes));
+            t.cm_glob = o->cm_glob;
+            t.cm_thr = uint16_t(o->rh.cm_thr);
+            t.cv_thr = uint16_t(o->rh.cv_thr);
+            t.mcls = cls < 0 ? 0 : 1;
+            t.k = uint8_t(cls < 0 ? 0 : cls);
+            terms.push_back(t);
+        }
+        if (terms.size() > first) terms.back().last = 1;
+    }
+    DevOp h;
+    std::memset(&h, 0, sizeof h);
+    h.kind = OP_PHASE;
+    h.b0 = -1;
+    h.b1 = int32_t(terms.size());
+    h.rh.code = RC_PH_GROUP;
+    out->push_back(h);
+    for (size_t i = 0; i < terms.size(); i += kTermsPerSlot) {
+        DevOp slot;
+        std::memset(&slot, 0, sizeof slot);
+        std::memcpy(&slot, terms.data() + i, sizeof(PhTerm) * std::min<size_t>(kTermsPerSlot, terms.size() - i));
+        out->push_back(slot);
+    }
+}
+
+// Replace runs of consecutive diagonal ops (which commute) by a merged group
+// of their groupable phases, the rest of the run after it, when the estimate
+// says the group costs less; then pad with NOP ops so that no group's header
+// and term slots straddle two staging chunks.
+bool merge_phase_groups(std::vector<DevOp>* ops_io, int coef_bytes, int nreg) {
+    std::vector<DevOp>& ops = *ops_io;
+    const int R = 1 << nreg;
+    const PhaseCost cost(coef_bytes);
+    constexpr int kMaxTerms = 15 * kTermsPerSlot;
+    std::vector<DevOp> out;
+    bool any = false;
+    size_t i = 0;
+    while (i < ops.size()) {
+        if (!is_diag_code(ops[i].rh.code)) {
+            out.push_back(ops[i++]);
+            continue;
+        }
+        size_t j = i;
+        while (j < ops.size() && is_diag_code(ops[j].rh.code)) ++j;
+        std::vector<const DevOp*> m, rest;
+        for (size_t k = i; k < j; ++k) (groupable(ops[k]) ? m : rest).push_back(&ops[k]);
+        for (size_t g0 = 0; g0 < m.size(); g0 += kMaxTerms) {
+            std::vector<const DevOp*> part(m.begin() + long(g0), m.begin() + long(std::min(m.size(), g0 + kMaxTerms)));
+            double now = 0.0, regs = 0.0;
+            uint32_t steps = 0;
+            for (const DevOp* o : part) {
+                now += cost.single(*o, R);
+                steps |= o->rh.mcls == 0 ? 1u : 2u << o->rh.a;
+            }
+            for (int b = 0; b <= nreg; ++b)
+                if ((steps >> b) & 1u) regs += b == 0 ? R : R / 2.0;
+            if (part.size() >= 2 && cost.group(int(part.size()), __builtin_popcount(steps), regs) < 0.9 * now) {
+                emit_group(&out, part, coef_bytes, nreg);
+                any = true;
+            } else
+                for (const DevOp* o : part) out.push_back(*o);
+        }
+        for (const DevOp* o : rest) out.push_back(*o);
+        i = j;
+    }
+    // pad: a group's header and its slots stay inside one chunk
+    std::vector<DevOp> padded;
+    padded.reserve(out.size());
+    for (size_t k = 0; k < out.size();) {
+        size_t len = 1;
+        if (out[k].rh.code == RC_PH_GROUP) len += size_t((out[k].b1 + kTermsPerSlot - 1) / kTermsPerSlot);
+        const size_t pos = padded.size() % kOpChunk;
+        if (pos + len > size_t(kOpChunk)) {
+            DevOp nop;
+            std::memset(&nop, 0, sizeof nop);
+            nop.kind = OP_PHASE;
+            nop.b0 = -1;
+            nop.rh.code = RC_NOP;
+            while (padded.size() % kOpChunk != 0) padded.push_back(nop);
+        }
+        for (size_t q = 0; q < len; ++q) padded.push_back(out[k + q]);
+        k += len;
+    }
+    ops.swap(padded);
+    return any;
+}
+
+}  // namespace
+
 // ------------------------------------------------ register-kernel layout --
 // The register kernel holds each tile bit on a lane-id bit, a register-index
 // bit or a warp-id bit.  The ops are walked in order, tracking that layout
@@ -460,9 +584,10 @@ void close_all(Bitset* W, const std::vector<Pass>& passes, const std::vector<Bit
 //  - every other op is resolved against the current layout: targets and
 //    conditions become physical bits, a flipped target exchanges the op's
 //    matrix entries (X U X), a flipped condition is marked in the value mask.
-void plan_register_layout(DevPass* dp, std::vector<DevOp>* ops_io, int coef_bytes, bool reorder) {
+void plan_register_layout(DevPass* dp, std::vector<DevOp>* ops_io, int coef_bytes, bool reorder, bool phase_groups) {
     const int tb = dp->lt + dp->nh;
     dp->reg_kernel = 0;
+    dp->groups = 0;
     if (tb < 7) return;
     const int nreg = std::min(5, std::max(2, tb - 8));
     const int nwarp = tb - 5 - nreg;
@@ -710,6 +835,7 @@ void plan_register_layout(DevPass* dp, std::vector<DevOp>* ops_io, int coef_byte
     }
     dp->fin = L;
     ops.swap(out);
+    if (phase_groups) dp->groups = merge_phase_groups(&ops, coef_bytes, nreg) ? 1 : 0;
 }
 
 }  // namespace qt

@@ -104,6 +104,8 @@ static uint32_t layout_index(const int8_t* lane, const int8_t* reg, const int8_t
     return j ^ flip;
 }
 
+static long g_groups = 0;  // merged phase groups seen
+
 static void run_planned(const std::vector<DevOp>& ops, const DevPass& dp, std::vector<cd>& T, uint64_t base) {
     Phys P{dp.nreg, dp.nwarp, 1 << dp.nreg, 1 << dp.nwarp, {}};
     P.v.assign(size_t(32) * P.R * P.W, 0.0);
@@ -113,8 +115,47 @@ static void run_planned(const std::vector<DevOp>& ops, const DevPass& dp, std::v
     for (int w = 0; w < P.W; ++w)
         for (int r = 0; r < P.R; ++r)
             for (int l = 0; l < 32; ++l) P.at(l, r, w) = T[layout_index(nullptr, reg0, warp0, P.nreg, P.nwarp, 0, l, r, w)];
-    for (const DevOp& o : ops) {
+    for (size_t oi = 0; oi < ops.size(); ++oi) {
+        const DevOp& o = ops[oi];
         const RegHdr& h = o.rh;
+        if (h.code == RC_PH_GROUP) {
+            // merged phases: per thread, the product of each step's terms whose
+            // conditions hold, applied to the step's registers
+            const int nt = o.b1;
+            const size_t nslots = size_t((nt + kTermsPerSlot - 1) / kTermsPerSlot);
+            if (nt < 1 || (oi % kOpChunk) + 1 + nslots > size_t(kOpChunk) || oi + nslots >= ops.size()) {
+                std::printf("malformed phase group at op %zu\n", oi);
+                std::exit(1);
+            }
+            const PhTerm* tm = reinterpret_cast<const PhTerm*>(&ops[oi + 1]);
+            for (int w = 0; w < P.W; ++w) {
+                for (int l = 0; l < 32; ++l) {
+                    const uint32_t ptid = uint32_t(l) | (uint32_t(w) << 5);
+                    for (int i = 0; i < nt;) {
+                        cd f = 1.0;
+                        bool go = false;
+                        int mcls = 0, k = 0;
+                        for (; i < nt; ++i) {
+                            const PhTerm& t = tm[i];
+                            if ((base & t.cm_glob) == t.cm_glob && ((ptid ^ t.cv_thr) & t.cm_thr) == t.cm_thr) {
+                                f *= cd(t.f.d[0], t.f.d[1]);
+                                go = true;
+                            }
+                            mcls = t.mcls;
+                            k = t.k;
+                            if (t.last) break;
+                        }
+                        ++i;
+                        if (go)
+                            for (int r = 0; r < P.R; ++r)
+                                if (mcls == 0 || ((r >> k) & 1)) P.at(l, r, w) *= f;
+                    }
+                }
+            }
+            oi += nslots;
+            ++g_groups;
+            continue;
+        }
         if (h.code == RC_PERM) {
             TileLayout from;
             std::memcpy(&from, &o.m, sizeof from);
@@ -231,9 +272,28 @@ int main(int argc, char** argv) {
         qt_set_option(c, "tile_high", th);
         qt_set_option(c, "merge", ci % 2);
         const int ngates = 120 + 20 * (ci % 5);
+        const bool ladder = ci % 5 == 4;  // QFT-like: H then controlled phases (runs of phases)
         for (int gi = 0; gi < ngates; ++gi) {
             qt_insert_level(c, gi);
             qt_gate g{};
+            if (ladder) {
+                const int j = (gi / n) % n, m = gi % n;
+                if (m == j) {
+                    g.kind = QT_H;
+                    g.ntarget = 1;
+                    g.target[0] = j;
+                } else {
+                    g.kind = (gi % 7 == 0) ? QT_CZ : QT_CP;
+                    g.ntarget = 1;
+                    g.target[0] = j;
+                    g.ncontrol = 1;
+                    g.control[0] = m;
+                    g.theta[0] = ang(rng);
+                }
+                qt_gate_id id;
+                if (qt_insert_gate(c, gi, &g, &id) != QT_OK) return 3;
+                continue;
+            }
             // weight permutations and phases: they exercise relabels and conditions
             static const int pool[] = {QT_H, QT_X, QT_X, QT_Y, QT_Z, QT_S, QT_SDG, QT_T, QT_RX, QT_RX, QT_RY, QT_RZ,
                                        QT_U3, QT_CNOT, QT_CNOT, QT_CZ, QT_SWAP, QT_SWAP, QT_CCX, QT_CP};
@@ -293,6 +353,10 @@ int main(int argc, char** argv) {
         }
         qt_destroy(c);
     }
-    std::printf("OK %ld %ld\n", npasses, nops);
+    if (g_groups == 0) {
+        std::printf("no merged phase group was planned\n");
+        return 1;
+    }
+    std::printf("OK %ld %ld %ld\n", npasses, nops, g_groups);
     return 0;
 }

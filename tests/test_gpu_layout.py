@@ -127,3 +127,44 @@ def test_passes_of_relabels_only(dtype, n, p):
         c.update_state(force_full=True)
         assert np.array_equal(a, c.read_amplitudes())
     c.close()
+
+
+@pytest.mark.parametrize("dtype", DTYPES)
+@pytest.mark.parametrize("opts", [{}, {"tile_high": 3}, {"tma": 1}])
+def test_merged_phase_groups(dtype, opts):
+    """Runs of phases (controlled-phase ladders with CZ, S, T, Z and phases
+    on qubits outside the tile, some behind relabeled X gates) merge into
+    one op per run; against the oracle, with incremental edits of a merged
+    phase bit-identical to a full re-simulation."""
+    n, p = 14, 9
+    rng = np.random.default_rng(41)
+    gates = []
+    for j in range(n):
+        gates.append(W.make_gate("h", [j]))
+        if j % 3 == 0:
+            gates.append(W.make_gate("x", [(j + 5) % n]))
+        for k in range(1, n):
+            m = (j + k) % n
+            name = ["cp", "cp", "cz", "cp"][k % 4]
+            par = [float(rng.uniform(0, 2 * math.pi))] if name == "cp" else []
+            gates.append(W.make_gate(name, [j, m], par))
+        for name in ("s", "t", "z"):
+            gates.append(W.make_gate(name, [int(rng.integers(n))]))
+    levels = prep_levels(n, seed=4) + W.asap_levels(n, gates)
+    c, ids = build_circuit(n, levels, dtype, p, **opts)
+    c.update_state()
+    want = oracle.simulate(n, W.flatten(levels))
+    assert max_err(c.read_amplitudes(), want) <= TOL[dtype]
+    for _ in range(3):
+        cand = [(l, k) for l, lv in enumerate(levels) for k, g in enumerate(lv) if g.name == "cp"]
+        l, k = cand[int(rng.integers(len(cand)))]
+        g = levels[l][k]
+        ng = g._replace(params=(g.params[0] + 0.3,))
+        ids[l][k] = c.replace_gate(l, ids[l][k], ng)
+        levels[l][k] = ng
+        c.update_state()
+        inc = c.read_amplitudes()
+        c.update_state(force_full=True)
+        assert np.array_equal(inc, c.read_amplitudes())
+    assert max_err(c.read_amplitudes(), oracle.simulate(n, W.flatten(levels))) <= TOL[dtype]
+    c.close()
