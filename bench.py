@@ -464,8 +464,32 @@ def run_deep30(args):
         "roofline": roofline_pair(achieved, peak, peak_kind, full["pass_kernel_alu_ops"], km, dtype, None,
                                   full["pass_kernel_launches"], f"{2 * bpa} B per amplitude per pass"),
     }
-    print(json.dumps(line), flush=True)
     c.close()
+    line["unfused"] = deep30_unfused(B, W, n, p, dtype, levels, peak, args.deep_unfused_gates)
+    print(json.dumps(line), flush=True)
+
+
+def deep30_unfused(B, W, n, p, dtype, levels, peak, ngates):
+    """The same kernel with fusion off: the first `ngates` gates of the
+    circuit, one gate per pass, so that each pass is bound by HBM rather
+    than by instruction issue.  Reports the passes' HBM bandwidth (bytes
+    read and written per pass over the event-timed kernel time) against the
+    measured peak, and the amplitude-update rate that fusion improves on."""
+    if ngates <= 0:
+        return None
+    gates = W.flatten(levels)[:ngates]
+    c = B.Circuit(n, dtype, p)
+    c.set_option("fusion", 0)
+    c.set_option("ckpt_interval", 1 << 20)
+    c.load_levels(W.asap_levels(n, gates))
+    c.update_state()
+    c.set_option("kernel_timing", 1)
+    st = min((c.update_state(force_full=True) for _ in range(2)), key=lambda s: s["pass_kernel_ms"])
+    c.close()
+    gbs = st["pass_kernel_bytes"] / (st["pass_kernel_ms"] * 1e-3) / 1e9
+    return {"gates": len(gates), "passes": st["passes_total"], "kernel_ms": st["pass_kernel_ms"],
+            "hbm_gbs": gbs, "hbm_frac_of_measured": gbs / peak if peak else None,
+            "amp_updates_per_s": st["amp_updates"] / (st["gpu_ms"] * 1e-3)}
 
 
 def run_serve(args):
@@ -735,6 +759,8 @@ def main():
                     help="served circuits checked against the plain complex128 path afterwards")
     ap.add_argument("--dtype", default="c128df", choices=["c128df", "c64", "c128"], help="deep30 only")
     ap.add_argument("--deep-ckpt", type=int, default=48, help="deep30: levels per checkpoint segment")
+    ap.add_argument("--deep-unfused-gates", type=int, default=64,
+                    help="deep30: gates timed one per pass (fusion off) for the HBM-bound view; 0 = skip")
     args = ap.parse_args()
     N_QUBITS, CKPT = args.n_qubits, args.ckpt
     if args.warmup < 3 and args.impl == "ours":
