@@ -381,14 +381,15 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
-def cpu_baseline(levels, budget_s=15.0, gates_cap=None):
+def cpu_baseline(levels, budget_s=15.0, gates_cap=None, n=None):
     """The FP64 oracle on the host cores: a prefix of the workload's circuit at
     full size, gate by gate, until the time budget is spent."""
     import oracle
     from paper_2210_01076_gb300 import workloads as W
+    n = N_QUBITS if n is None else n
     gates = W.flatten(levels)
     nth = oracle.max_threads()
-    psi = np.zeros(1 << N_QUBITS, np.complex128)
+    psi = np.zeros(1 << n, np.complex128)
     psi[0] = 1.0
     done = 0
     t0 = time.perf_counter()
@@ -398,8 +399,8 @@ def cpu_baseline(levels, budget_s=15.0, gates_cap=None):
         if time.perf_counter() - t0 > budget_s or (gates_cap and done >= gates_cap):
             break
     dt = time.perf_counter() - t0
-    return {"value": done * (1 << N_QUBITS) / dt, "unit": "amp-updates/s", "cores": nth, "kind": "oracle",
-            "sample": f"first {done} gates of the n=24 circuit, full state, FP64 textbook loops ({dt:.1f} s)"}
+    return {"value": done * (1 << n) / dt, "unit": "amp-updates/s", "cores": nth, "kind": "oracle",
+            "sample": f"first {done} gates of the n={n} circuit, full state, FP64 textbook loops ({dt:.1f} s)"}
 
 
 # ------------------------------------------------------------- reference --
@@ -466,6 +467,8 @@ def run_deep30(args):
     }
     c.close()
     line["unfused"] = deep30_unfused(B, W, n, p, dtype, levels, peak, args.deep_unfused_gates)
+    if args.deep_oracle_s > 0:
+        line["cpu_baseline"] = cpu_baseline(levels, budget_s=args.deep_oracle_s, n=n)
     print(json.dumps(line), flush=True)
 
 
@@ -759,6 +762,8 @@ def main():
                     help="served circuits checked against the plain complex128 path afterwards")
     ap.add_argument("--dtype", default="c128df", choices=["c128df", "c64", "c128"], help="deep30 only")
     ap.add_argument("--deep-ckpt", type=int, default=48, help="deep30: levels per checkpoint segment")
+    ap.add_argument("--deep-oracle-s", type=float, default=15.0,
+                    help="deep30: seconds of FP64 oracle on the host cores (a prefix of the circuit); 0 = skip")
     ap.add_argument("--deep-unfused-gates", type=int, default=64,
                     help="deep30: gates timed one per pass (fusion off) for the HBM-bound view; 0 = skip")
     args = ap.parse_args()

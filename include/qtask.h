@@ -119,8 +119,9 @@ typedef struct {
 } qt_update_stats;
 
 /* Create an empty circuit (no levels) whose state is |0...0>.
- * n_qubits in [1, 34]; log2_partition in [0, n_qubits] (partition size
- * 2^log2_partition amplitudes, the paper's block size B, Section III-C).
+ * n_qubits in [1, 34]; log2_partition in [max(0, n_qubits - 30), n_qubits]
+ * (partition size 2^log2_partition amplitudes, the paper's block size B,
+ * Section III-C; at most 2^30 partitions).
  * Allocates host memory only.  *out receives the handle. */
 qt_status qt_create(int32_t n_qubits, int32_t dtype, int32_t log2_partition, qt_circuit** out);
 

@@ -226,3 +226,48 @@ def test_batch256_full_size_sampled_circuits_against_oracle():
     batch.close()
     for c in circs:
         c.close()
+
+
+@pytest.mark.parametrize("n,dtype", [(33, "c64"), (32, "c128df")])
+def test_largest_states_indices_past_2_to_32(n, dtype):
+    """The largest states that fit the device with one segment (64 GiB per
+    buffer): GHZ and the QFT of a basis state, checked at sampled blocks on
+    both sides of amplitude 2^32 (2^31 at n = 32; byte offsets pass 2^32
+    there) and at the ends; FP64 norm."""
+    N = 1 << n
+    mid = min(1 << 32, N // 2)
+    starts = [0, mid - BLOCK, mid, N - BLOCK] + [
+        int(b) * BLOCK for b in np.random.default_rng(n).choice(N // BLOCK, size=6, replace=False)]
+    ghz = [W.make_gate("h", [0])] + [W.make_gate("cnot", [q + 1, q]) for q in range(n - 1)]
+    c = B.Circuit(n, dtype, 20)
+    c.set_option("ckpt_interval", 1 << 20)
+    c.load_levels(W.asap_levels(n, ghz))
+    c.update_state()
+    for s in starts:
+        want = np.zeros(BLOCK)
+        if s == 0:
+            want[0] = 1 / math.sqrt(2)
+        if s == N - BLOCK:
+            want[-1] = 1 / math.sqrt(2)
+        assert max_err(c.read_amplitudes(s, BLOCK), want) <= TOL[dtype], s
+    assert abs(c.norm() - 1.0) <= TOL[dtype]
+    c.close()
+    x = 0x15A5F3C71 & (N - 1)
+    gates = [W.make_gate("x", [q]) for q in range(n) if x >> q & 1]
+    for j in range(n - 1, -1, -1):
+        gates.append(W.make_gate("h", [j]))
+        for m in range(j - 1, -1, -1):
+            gates.append(W.make_gate("cp", [j, m], [math.pi / (1 << (j - m))]))
+    gates += [W.make_gate("swap", [i, n - 1 - i]) for i in range(n // 2)]
+    c = B.Circuit(n, dtype, 20)
+    c.set_option("ckpt_interval", 1 << 20)
+    c.load_levels(W.asap_levels(n, gates))
+    c.update_state()
+    mag = 2.0 ** (-n / 2)
+    for s in starts:
+        y = np.arange(s, s + BLOCK, dtype=np.uint64)
+        ph = (np.uint64(x) * y) & np.uint64(N - 1)  # the product wraps mod 2^64, a multiple of 2^n
+        want = mag * np.exp(2j * math.pi * ph.astype(np.float64) / N)
+        err = max_err(c.read_amplitudes(s, BLOCK), want)
+        assert err <= TOL[dtype] and err <= rel_tol(dtype) * mag, (s, err)
+    c.close()
