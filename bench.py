@@ -417,12 +417,24 @@ def run_deep30(args):
     from paper_2210_01076_gb300 import workloads as W
     qbuild.build()
     B.load()
+    from paper_2210_01076_gb300 import tuning
     n, ngates, p = 30, 2000, 18
     dtype = args.dtype
     levels = W.qft_like_circuit(n, ngates, seed=7)
+    tuned = None
+    if args.deep_tune:
+        # the fusion width (qubits a tile holds above its low run), timed 1..5
+        # on full simulations without checkpoints; the best one is used below
+        t = tuning.tune_circuit(n, dtype, levels, p, tile_high=range(1, 6), ckpt_interval=(1 << 20,),
+                                merge=(1,), repeats=1)
+        if t["best"]:
+            tuned = {"tile_high": t["best"]["options"]["tile_high"],
+                     "full_ms": {str(r["options"]["tile_high"]): r.get("full_ms") for r in t["table"]}}
     stream = torch.cuda.Stream()
     c = B.Circuit(n, dtype, p)
     c.set_stream(stream.cuda_stream)
+    if tuned:
+        c.set_option("tile_high", tuned["tile_high"])
     ckpt = args.deep_ckpt
     c.set_option("ckpt_interval", ckpt)
     for kv in args.option:
@@ -456,7 +468,8 @@ def run_deep30(args):
         "value": full["amp_updates"] / (full["gpu_ms"] * 1e-3), "unit": "amp-updates/s",
         "dtype": {"c64": "c64 (fp32)", "c128df": "c128 (float-float)", "c128": "c128 (fp64)"}[dtype],
         "config": {"workload": "QFT-like n=30, 2000 gates, partitions 2^18", "ckpt_interval_levels": ckpt,
-                   "levels": L, "segments": full["segments_total"], "passes": full["passes_total"]},
+                   "levels": L, "segments": full["segments_total"], "passes": full["passes_total"],
+                   "fusion_width_tuned": tuned},
         "full_sim_ms": full["gpu_ms"], "hbm_gbs": full["hbm_bytes"] / (full["gpu_ms"] * 1e-3) / 1e9,
         "incremental_latency_ms": {"p50": pctl([s["gpu_ms"] for s in inc], 50),
                                    "p99": pctl([s["gpu_ms"] for s in inc], 99)},
@@ -665,6 +678,14 @@ def run_batch(args):
         ids.append(c.load_levels(lvls))
         levels.append([list(x) for x in lvls])
         circs.append(c)
+    tuned = None
+    if args.batch_tune:
+        # the fusion width of every circuit of the batch, timed 3..5
+        from paper_2210_01076_gb300 import tuning
+        t = tuning.tune_batch(circs, tile_high=(3, 4, 5))
+        if t["best"]:
+            tuned = {"tile_high": t["best"]["tile_high"],
+                     "round_ms": {str(r["tile_high"]): r.get("round_ms") for r in t["table"]}}
     batch = B.Batch(circs)
     first = batch.run()
     capture = batch.run()
@@ -689,6 +710,7 @@ def run_batch(args):
             "value": amp / (np.median(ms) * 1e-3), "unit": "amp-updates/s",
             "config": {"circuits": len(circs), "qubits": "10-20", "depth": "50-400",
                        "gates_total": int(sum(c.num_gates() for c in circs)), "passes": rounds[-1]["passes"],
+                       "fusion_width_tuned": tuned,
                        "tiles_per_launch": rounds[-1]["tiles"]},
             "first_run_ms": first["gpu_ms"], "capture_run_ms": capture["gpu_ms"],
             "round_ms": {"p50": pctl(ms, 50), "p99": pctl(ms, 99)},
@@ -753,6 +775,7 @@ def main():
     ap.add_argument("--workload", default="incremental24", choices=["incremental24", "deep30", "serve", "batch"])
     ap.add_argument("--batch-circuits", type=int, default=256)
     ap.add_argument("--batch-rounds", type=int, default=10)
+    ap.add_argument("--batch-tune", type=int, default=1, help="batch: autotune the fusion width (tile_high 3..5)")
     ap.add_argument("--serve-circuits", type=int, default=64)
     ap.add_argument("--serve-workers", type=int, default=8)
     ap.add_argument("--serve-budget-gb", type=float, default=150.0)
@@ -762,6 +785,7 @@ def main():
                     help="served circuits checked against the plain complex128 path afterwards")
     ap.add_argument("--dtype", default="c128df", choices=["c128df", "c64", "c128"], help="deep30 only")
     ap.add_argument("--deep-ckpt", type=int, default=48, help="deep30: levels per checkpoint segment")
+    ap.add_argument("--deep-tune", type=int, default=1, help="deep30: autotune the fusion width (tile_high 1..5)")
     ap.add_argument("--deep-oracle-s", type=float, default=15.0,
                     help="deep30: seconds of FP64 oracle on the host cores (a prefix of the circuit); 0 = skip")
     ap.add_argument("--deep-unfused-gates", type=int, default=64,
