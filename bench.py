@@ -437,6 +437,9 @@ def run_deep30(args):
         c.set_option("tile_high", tuned["tile_high"])
     ckpt = args.deep_ckpt
     c.set_option("ckpt_interval", ckpt)
+    if args.deep_ckpt_budget_gb > 0:
+        # as many checkpoints as the budget holds (the library sets the interval)
+        c.set_option("ckpt_budget", int(args.deep_ckpt_budget_gb * 1e9))
     for kv in args.option:
         k, v = kv.split("=")
         c.set_option(k, int(v))
@@ -467,7 +470,9 @@ def run_deep30(args):
         "metric": "amplitude-updates/s", "workload": "deep30",
         "value": full["amp_updates"] / (full["gpu_ms"] * 1e-3), "unit": "amp-updates/s",
         "dtype": {"c64": "c64 (fp32)", "c128df": "c128 (float-float)", "c128": "c128 (fp64)"}[dtype],
-        "config": {"workload": "QFT-like n=30, 2000 gates, partitions 2^18", "ckpt_interval_levels": ckpt,
+        "config": {"workload": "QFT-like n=30, 2000 gates, partitions 2^18",
+                   "ckpt_interval_levels": -(-L // full["segments_total"]) if args.deep_ckpt_budget_gb > 0 else ckpt,
+                   "ckpt_budget_gb": args.deep_ckpt_budget_gb or None,
                    "levels": L, "segments": full["segments_total"], "passes": full["passes_total"],
                    "fusion_width_tuned": tuned},
         "full_sim_ms": full["gpu_ms"], "hbm_gbs": full["hbm_bytes"] / (full["gpu_ms"] * 1e-3) / 1e9,
@@ -785,6 +790,8 @@ def main():
                     help="served circuits checked against the plain complex128 path afterwards")
     ap.add_argument("--dtype", default="c128df", choices=["c128df", "c64", "c128"], help="deep30 only")
     ap.add_argument("--deep-ckpt", type=int, default=48, help="deep30: levels per checkpoint segment")
+    ap.add_argument("--deep-ckpt-budget-gb", type=float, default=200.0,
+                    help="deep30: device memory for the state and checkpoints (sets the interval); 0 = --deep-ckpt")
     ap.add_argument("--deep-tune", type=int, default=1, help="deep30: autotune the fusion width (tile_high 1..5)")
     ap.add_argument("--deep-oracle-s", type=float, default=15.0,
                     help="deep30: seconds of FP64 oracle on the host cores (a prefix of the circuit); 0 = skip")

@@ -236,6 +236,11 @@ qt_status qt_norm_static(const void* amps_device, uint64_t count, int32_t dtype,
 
 /* Options (value semantics):
  *   "ckpt_interval"  levels per checkpoint segment (>= 1; default 4)
+ *   "ckpt_budget"    > 0: bytes of device memory for the state and its
+ *                    checkpoints (one state vector each); the interval is
+ *                    then the smallest whose checkpoints fit (Section III-F's
+ *                    per-net states, as many as the memory holds), kept across
+ *                    updates while it still fits; 0 (default): ckpt_interval
  *   "fusion"         0: one gate per pass; 1: tile fusion (default)
  *   "tile_high"      max qubits at or above the tile's low bits per pass (0..7)
  *   "mem_limit"      device-memory budget in bytes for state + checkpoints (0 = none)
@@ -252,7 +257,8 @@ qt_status qt_norm_static(const void* amps_device, uint64_t count, int32_t dtype,
  *   "dry_run"        1: qt_update_state plans and tracks but launches nothing and
  *                    allocates nothing (host-logic testing); the device state is
  *                    marked stale and the next real update runs in full.
- * Changing ckpt_interval, fusion or tile_high makes the next update full. */
+ * Changing ckpt_interval, fusion or tile_high (or a budget that changes the
+ * interval) makes the next update full. */
 qt_status qt_set_option(qt_circuit* c, const char* key, int64_t value);
 
 /* Run the circuit's GPU work on `cuda_stream` (a cudaStream_t; NULL = the

@@ -86,6 +86,7 @@ struct qt_circuit {
 
     // options
     int ckpt_interval = 4;
+    int64_t ckpt_budget = 0;  // > 0: bytes for the state and checkpoints; sets the interval
     bool fusion = true;
     bool merge = true;
     int tile_high = 5;  // tiles of 2^11 (complex128) / 2^12 (complex64) amplitudes
@@ -409,6 +410,20 @@ cudaEvent_t pool_event(qt_circuit* c, size_t i) {
     return c->ev_pool[i];
 }
 
+// Levels per checkpoint segment.  With a checkpoint budget: the interval of
+// the current plan while its slabs (one per segment plus the initial state)
+// still fit, else the smallest interval whose slabs fit (a new interval
+// makes the next update full).
+int effective_interval(const qt_circuit* c) {
+    if (c->ckpt_budget <= 0) return c->ckpt_interval;
+    const int64_t L = int64_t(c->levels.size());
+    const int64_t slabs = std::max<int64_t>(2, c->ckpt_budget / int64_t(c->state_bytes()));
+    auto fits = [&](int64_t G) { return (L + G - 1) / G + 1 <= slabs; };
+    if (c->have_plan && c->plan_G > 0 && fits(c->plan_G)) return c->plan_G;
+    const int64_t G = std::max<int64_t>(1, (L + slabs - 2) / (slabs - 1));
+    return int(std::min<int64_t>(G, 1 << 20));
+}
+
 qt_status do_update(qt_circuit* c, int force_full, qt_update_stats* stats) {
     auto t0 = std::chrono::steady_clock::now();
     qt_update_stats st;
@@ -418,7 +433,7 @@ qt_status do_update(qt_circuit* c, int force_full, qt_update_stats* stats) {
 
     // ---- plan
     const PlanParams pp = make_params(c);
-    const int G = c->ckpt_interval;
+    const int G = effective_interval(c);
     const int L = int(c->levels.size());
     const int S = (L + G - 1) / G;
     std::vector<SegPlan> nplans(S);
@@ -1087,6 +1102,9 @@ qt_status qt_set_option(qt_circuit* c, const char* key, int64_t value) {
     if (k == "ckpt_interval") {
         if (value < 1 || value > (1 << 20)) return fail(c, QT_ERR_ARG, "ckpt_interval must be >= 1");
         c->ckpt_interval = int(value);
+    } else if (k == "ckpt_budget") {
+        if (value < 0) return fail(c, QT_ERR_ARG, "ckpt_budget must be >= 0");
+        c->ckpt_budget = value;
     } else if (k == "fusion") {
         c->fusion = value != 0;
     } else if (k == "merge") {
@@ -1178,7 +1196,8 @@ size_t qt::circuit_device_bytes(const qt_circuit* c) {
 
 size_t qt::circuit_device_need(const qt_circuit* c) {
     const size_t L = c->levels.size();
-    const size_t S = (L + size_t(c->ckpt_interval) - 1) / size_t(c->ckpt_interval);
+    const size_t G = size_t(effective_interval(c));
+    const size_t S = (L + G - 1) / G;
     return (S + 2) * c->state_bytes();  // checkpoints, and a level's worth of slack for inserted levels
 }
 

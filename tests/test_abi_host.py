@@ -235,3 +235,34 @@ def test_planner_makes_progress_when_a_gate_exceeds_the_tile(tile_high):
     c.load_levels(levels)
     st = c.update_state()
     assert st["passes_total"] >= 3 and st["amp_updates"] == 4 * (1 << n)
+
+
+def test_checkpoint_budget_sets_the_interval():
+    """ckpt_budget: the interval is the smallest whose checkpoints (one state
+    vector per segment, plus the initial state) fit the budget, and it stays
+    while it still fits (dry runs: planning only)."""
+    n = 16
+    state = (1 << n) * 8  # complex64
+    c = B.Circuit(n, "c64", 10)
+    c.set_option("dry_run", 1)
+    c.set_option("ckpt_budget", 11 * state)  # 11 state vectors: at most 10 segments
+
+    def seg_sizes():
+        return [c.segment_info(s)["nlevels"] for s in range(c.num_segments())]
+
+    c.load_levels([[W.make_gate("h", [l % n])] for l in range(85)])
+    c.update_state()
+    assert max(seg_sizes()) == 9 and len(seg_sizes()) == 10 and sum(seg_sizes()) == 85
+    c.load_levels([[W.make_gate("x", [l % n])] for l in range(5)])
+    c.update_state()  # 90 levels still fit at 9 per segment: kept
+    assert max(seg_sizes()) == 9 and len(seg_sizes()) == 10 and sum(seg_sizes()) == 90
+    c.load_levels([[W.make_gate("x", [0])]])
+    c.update_state()  # 91 levels at 9 would need 12 vectors: 10 per segment
+    assert max(seg_sizes()) == 10 and len(seg_sizes()) == 10 and sum(seg_sizes()) == 91
+    c.set_option("ckpt_budget", 0)
+    c.set_option("ckpt_interval", 5)
+    c.update_state()
+    assert len(seg_sizes()) == 19
+    with pytest.raises(B.QtError):
+        c.set_option("ckpt_budget", -1)
+    c.close()
