@@ -85,10 +85,10 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-def profiled_traffic(kernel_hash):
-    """DRAM bytes per launch of the dominant kernel from the committed ncu
-    summary, if it was taken on the current kernel source."""
-    path = os.path.join(ROOT, "profiles", "k_pass_df_traffic.json")
+def profiled_traffic(kernel_hash, name="k_pass_df_traffic.json"):
+    """DRAM bytes per amplitude-pass of the fused-pass kernel from a committed
+    ncu summary, if it was taken on the current kernel source."""
+    path = os.path.join(ROOT, "profiles", name)
     try:
         with open(path) as f:
             d = json.load(f)
@@ -418,7 +418,8 @@ def run_deep30(args):
     qbuild.build()
     B.load()
     from paper_2210_01076_gb300 import tuning
-    n, ngates, p = 30, 2000, 18
+    n, ngates = args.deep_n, 2000
+    p = min(18, n)
     dtype = args.dtype
     levels = W.qft_like_circuit(n, ngates, seed=7)
     tuned = None
@@ -466,11 +467,19 @@ def run_deep30(args):
     kb, km = full["pass_kernel_bytes"], full["pass_kernel_ms"]
     achieved = kb / (km * 1e-3) / 1e9 if km > 0 else None
     bpa = 8 if dtype == "c64" else 16
+    traffic_per_launch = None
+    if dtype == "c64" and full["pass_kernel_launches"]:
+        # ncu DRAM bytes per amplitude-pass of the complex64 instantiation
+        # (captured on a smaller state of the same circuit family), scaled to
+        # this run's average launch
+        t = profiled_traffic(kernel_source_hash(), "k_pass_c64_traffic.json")
+        if t:
+            traffic_per_launch = t["dram_bytes_per_amp_pass"] * (kb / (2 * bpa)) / full["pass_kernel_launches"]
     line = {
         "metric": "amplitude-updates/s", "workload": "deep30",
         "value": full["amp_updates"] / (full["gpu_ms"] * 1e-3), "unit": "amp-updates/s",
         "dtype": {"c64": "c64 (fp32)", "c128df": "c128 (float-float)", "c128": "c128 (fp64)"}[dtype],
-        "config": {"workload": "QFT-like n=30, 2000 gates, partitions 2^18",
+        "config": {"workload": f"QFT-like n={n}, 2000 gates, partitions 2^{p}",
                    "ckpt_interval_levels": -(-L // full["segments_total"]) if args.deep_ckpt_budget_gb > 0 else ckpt,
                    "ckpt_budget_gb": args.deep_ckpt_budget_gb or None,
                    "levels": L, "segments": full["segments_total"], "passes": full["passes_total"],
@@ -480,7 +489,7 @@ def run_deep30(args):
                                    "p99": pctl([s["gpu_ms"] for s in inc], 99)},
         "clean_fraction_mean": float(np.mean([s["clean_fraction"] for s in inc])) if inc else None,
         "norm": norm,
-        "roofline": roofline_pair(achieved, peak, peak_kind, full["pass_kernel_alu_ops"], km, dtype, None,
+        "roofline": roofline_pair(achieved, peak, peak_kind, full["pass_kernel_alu_ops"], km, dtype, traffic_per_launch,
                                   full["pass_kernel_launches"], f"{2 * bpa} B per amplitude per pass"),
     }
     c.close()
@@ -795,6 +804,7 @@ def main():
     ap.add_argument("--deep-tune", type=int, default=1, help="deep30: autotune the fusion width (tile_high 1..5)")
     ap.add_argument("--deep-oracle-s", type=float, default=15.0,
                     help="deep30: seconds of FP64 oracle on the host cores (a prefix of the circuit); 0 = skip")
+    ap.add_argument("--deep-n", type=int, default=30, help="deep30: qubits (smaller cases for profiling only)")
     ap.add_argument("--deep-unfused-gates", type=int, default=64,
                     help="deep30: gates timed one per pass (fusion off) for the HBM-bound view; 0 = skip")
     args = ap.parse_args()
