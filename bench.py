@@ -155,6 +155,18 @@ class ClockSampler:
         return out
 
 
+# The paper's own results, quoted for context only: they are CPU wall-clock
+# ratios of its simulator over two others on QASMBench circuits (Table 3,
+# ratios of summed runtimes), not amplitude-updates/s, so no ratio is
+# computed against them.
+PAPER_CONTEXT = {
+    "hardware": "16 Intel i7 cores at 2.50 GHz, 128 GB RAM (CPU only)",
+    "speedup_full": {"vs_qulacs": 1.46, "vs_qiskit": 1.71},
+    "speedup_incremental": {"vs_qulacs": 5.77, "vs_qiskit": 9.76},
+    "source": "Table 3 (20 QASMBench circuits, block size 256, 16 threads)",
+}
+
+
 def make_workload(seed, rounds):
     from paper_2210_01076_gb300 import workloads as W
     levels = W.random_circuit(N_QUBITS, N_GATES, seed=seed, p_multi=P_MULTI)
@@ -372,6 +384,7 @@ def run_ours(args):
                     "note": "edits in, qt_update_state, whole state read to pinned host memory each step (qt_read_amplitudes_async: the copy of step k overlaps step k+1; the last is waited for in the timed region)"},
             "clocks": clocks,
             "wall_s_timed": t_wall,
+            "paper_context": PAPER_CONTEXT,
         }
         if cpu is not None:
             line["cpu_baseline"] = cpu
