@@ -394,9 +394,10 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
-def cpu_baseline(levels, budget_s=15.0, gates_cap=None, n=None):
+def cpu_baseline(levels, budget_s=15.0, gates_cap=None, n=None, keep=None):
     """The FP64 oracle on the host cores: a prefix of the workload's circuit at
-    full size, gate by gate, until the time budget is spent."""
+    full size, gate by gate, until the time budget is spent.  With a dict
+    `keep`, the oracle's state and the gates it applied are left in it."""
     import oracle
     from paper_2210_01076_gb300 import workloads as W
     n = N_QUBITS if n is None else n
@@ -412,8 +413,32 @@ def cpu_baseline(levels, budget_s=15.0, gates_cap=None, n=None):
         if time.perf_counter() - t0 > budget_s or (gates_cap and done >= gates_cap):
             break
     dt = time.perf_counter() - t0
+    if keep is not None:
+        keep.update(psi=psi, gates=gates[:done])
     return {"value": done * (1 << n) / dt, "unit": "amp-updates/s", "cores": nth, "kind": "oracle",
             "sample": f"first {done} gates of the n={n} circuit, full state, FP64 textbook loops ({dt:.1f} s)"}
+
+
+def oracle_prefix_accuracy(B, W, n, p, dtype, keep, tol):
+    """The library against the FP64 oracle on the prefix of the circuit that
+    the oracle simulated for the CPU baseline: the same gates in a fresh
+    circuit, one full update, the max-abs amplitude error over the whole
+    state (read back in chunks)."""
+    psi, gates = keep["psi"], keep["gates"]
+    c = B.Circuit(n, dtype, p)
+    try:
+        c.set_option("ckpt_interval", 1 << 20)  # one segment: state + output only
+        c.load_levels(W.asap_levels(n, gates))
+        c.update_state()
+        err, chunk = 0.0, 1 << 24
+        for first in range(0, 1 << n, chunk):
+            cnt = min(chunk, (1 << n) - first)
+            a = c.read_amplitudes(first, cnt).astype(np.complex128)
+            err = max(err, float(np.max(np.abs(a - psi[first:first + cnt]))))
+    finally:
+        c.close()
+    return {"gates": len(gates), "max_abs_err_vs_fp64_oracle": err, "tolerance": tol,
+            "note": "the oracle's prefix of the circuit (the CPU-baseline sample), whole state"}
 
 
 # ------------------------------------------------------------- reference --
@@ -508,7 +533,10 @@ def run_deep30(args):
     c.close()
     line["unfused"] = deep30_unfused(B, W, n, p, dtype, levels, peak, args.deep_unfused_gates)
     if args.deep_oracle_s > 0:
-        line["cpu_baseline"] = cpu_baseline(levels, budget_s=args.deep_oracle_s, n=n)
+        keep = {}
+        line["cpu_baseline"] = cpu_baseline(levels, budget_s=args.deep_oracle_s, n=n, keep=keep)
+        line["accuracy"] = oracle_prefix_accuracy(B, W, n, p, dtype, keep, 1e-5 if dtype == "c64" else 1e-12)
+        keep.clear()
     print(json.dumps(line), flush=True)
 
 
