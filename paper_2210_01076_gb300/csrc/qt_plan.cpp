@@ -609,9 +609,10 @@ void plan_register_layout(DevPass* dp, std::vector<DevOp>* ops_io, int coef_byte
     auto pc = [](uint32_t x) { return __builtin_popcount(x); };
     std::vector<char> done(ops.size(), 0);
     // register set of a new layout for op i and the ops not yet placed after
-    // it: their targets above the lanes
+    // it: their targets above the lanes.  A pass whose ops all merged into
+    // identities has none: its layout is just the highest tile bits.
     auto choose = [&](size_t i, uint32_t keep) -> uint32_t {
-        uint32_t s = targets(ops[i]) & upper;
+        uint32_t s = i < ops.size() ? targets(ops[i]) & upper : 0u;
         for (size_t j = 0; j < ops.size(); ++j) {
             if (j == i || done[j] || relabel(ops[j])) continue;
             const uint32_t t = s | (targets(ops[j]) & upper);

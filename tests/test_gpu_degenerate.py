@@ -102,3 +102,32 @@ def test_removing_every_gate_returns_to_the_zero_state(dtype):
     c.update_state()
     assert np.array_equal(c.read_amplitudes().astype(np.complex128), basis_zero(n))
     c.close()
+
+
+@pytest.mark.parametrize("dtype", DTYPES)
+def test_passes_whose_gates_cancel_copy_the_state(dtype):
+    """Segments holding only a gate and its inverse on one qubit: merged into
+    an exact identity and dropped, the fused pass has no ops and copies its
+    partitions from one checkpoint to the next.  Edits that make such a pass
+    non-empty and empty again stay bit-identical to a full re-simulation."""
+    n, p = 12, 8
+    levels = [list(lv) for lv in W.random_circuit(n, 40, seed=41, p_multi=0.4)]
+    if len(levels) % 2:
+        levels.append([W.make_gate("rz", [0], [0.3])])
+    first_pair = len(levels)
+    for a, b in [("h", "h"), ("z", "z"), ("s", "sdg"), ("t", "tdg"), ("x", "x")]:
+        levels += [[W.make_gate(a, [3])], [W.make_gate(b, [3])]]
+    levels += [list(lv) for lv in W.random_circuit(n, 40, seed=42, p_multi=0.4)]
+    c, ids = build_circuit(n, levels, dtype, p, ckpt_interval=2)  # one pair per segment
+    c.update_state()
+    assert max_err(c.read_amplitudes(), oracle.simulate(n, W.flatten(levels))) <= TOL[dtype]
+    model = [list(lv) for lv in levels]
+    for g in (W.make_gate("rx", [3], [0.7]), W.make_gate("h", [3])):
+        ids[first_pair][0] = c.replace_gate(first_pair, ids[first_pair][0], g)
+        model[first_pair][0] = g
+        c.update_state()
+        inc = c.read_amplitudes()
+        assert max_err(inc, oracle.simulate(n, W.flatten(model))) <= TOL[dtype]
+        c.update_state(force_full=True)
+        assert np.array_equal(inc, c.read_amplitudes())
+    c.close()
