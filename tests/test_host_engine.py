@@ -8,7 +8,10 @@ and the scheduler run, nothing is launched or allocated).
   test instead of ending the test run.
 - The serving loop runs requests of different circuits concurrently on its
   worker threads, but each circuit's requests in submission order, and fails
-  a request whose circuit can never fit the memory budget."""
+  a request whose circuit can never fit the memory budget.
+- Random edit streams (every edit kind, gate-and-inverse pairs, option
+  changes, forced full updates) over random qubit counts, partition sizes
+  and dtypes plan without error and keep the circuit's gate count."""
 import os
 import subprocess
 import sys
@@ -101,4 +104,75 @@ def test_server_runs_each_circuits_requests_in_order():
         srv.close()
         for c in circs:
             c.close()
+    """)
+
+
+def test_random_edit_streams_plan_without_errors():
+    run_child("""
+        def scenario(sc):
+            rng = np.random.default_rng(sc)
+            n = int(rng.integers(1, 17))
+            p = int(rng.integers(0, n + 1))
+            c = B.Circuit(n, ["c128", "c64", "c128df"][sc % 3], p)
+
+            def opt(k, v):
+                try:
+                    c.set_option(k, v)
+                except B.QtError:  # e.g. a tile too large for the dtype
+                    pass
+            opt("dry_run", 1)
+            opt("ckpt_interval", int(rng.integers(1, 6)))
+            for k, hi in (("fusion", 2), ("merge", 2), ("tile_high", 8), ("reg_kernel", 2)):
+                if rng.random() < 0.3:
+                    opt(k, int(rng.integers(0, hi)))
+            pm = None if n < 3 else 0.4
+            levels = W.random_circuit(n, int(rng.integers(0, 120)), seed=sc, p_multi=pm) if n >= 3 else []
+            ids = c.load_levels(levels)
+            model = [list(lv) for lv in levels]
+            c.update_state()
+            for _ in range(int(rng.integers(1, 12))):
+                for _ in range(int(rng.integers(1, 6))):
+                    L, r = c.num_levels(), rng.random()
+                    if r < 0.3 or L == 0:
+                        lv = int(rng.integers(L + 1))
+                        g = W.random_gate(rng, n, pm) if n >= 3 else W.make_gate("h", [0])
+                        c.insert_level(lv)
+                        ids.insert(lv, [c.insert_gate(lv, g)])
+                        model.insert(lv, [g])
+                    elif r < 0.55:
+                        lv = int(rng.integers(L))
+                        if ids[lv]:
+                            k = int(rng.integers(len(ids[lv])))
+                            c.remove_gate(lv, ids[lv][k])
+                            del ids[lv][k], model[lv][k]
+                    elif r < 0.75:
+                        lv = int(rng.integers(L))
+                        if ids[lv]:
+                            k = int(rng.integers(len(ids[lv])))
+                            q = list(model[lv][k].qubits)
+                            same = [nm for nm in W.ALL_KINDS if sum(W.ARITY[nm][:2]) == len(q)]
+                            nm = same[int(rng.integers(len(same)))]
+                            ng = W.make_gate(nm, q, rng.uniform(0, 6.28, W.ARITY[nm][2]))
+                            ids[lv][k] = c.replace_gate(lv, ids[lv][k], ng)
+                            model[lv][k] = ng
+                    elif r < 0.85:
+                        lv = int(rng.integers(L))
+                        c.remove_level(lv)
+                        del ids[lv], model[lv]
+                    else:  # a gate and its inverse in two fresh levels
+                        lv = int(rng.integers(L + 1))
+                        g = W.random_gate(rng, n, pm) if n >= 3 else W.make_gate("x", [0])
+                        c.insert_level(lv)
+                        c.insert_level(lv)
+                        ids[lv:lv] = [[c.insert_gate(lv, g)], [c.insert_gate(lv + 1, W.inverse_gate(g))]]
+                        model[lv:lv] = [[g], [W.inverse_gate(g)]]
+                if rng.random() < 0.1:
+                    opt("ckpt_interval", int(rng.integers(1, 6)))
+                st = c.update_state(force_full=bool(rng.random() < 0.1))
+                assert st["gates_total"] == sum(len(lv) for lv in model), sc
+                assert c.num_levels() == len(model), sc
+            c.close()
+
+        for sc in range(120):
+            scenario(sc)
     """)
