@@ -125,6 +125,8 @@ def test_random_edit_streams_plan_without_errors():
             for k, hi in (("fusion", 2), ("merge", 2), ("tile_high", 8), ("reg_kernel", 2)):
                 if rng.random() < 0.3:
                     opt(k, int(rng.integers(0, hi)))
+            if rng.random() < 0.3:  # checkpoints sized from a budget of state vectors
+                opt("ckpt_budget", int(rng.integers(0, 40)) * (1 << n) * 16)
             pm = None if n < 3 else 0.4
             levels = W.random_circuit(n, int(rng.integers(0, 120)), seed=sc, p_multi=pm) if n >= 3 else []
             ids = c.load_levels(levels)
@@ -171,6 +173,8 @@ def test_random_edit_streams_plan_without_errors():
                 st = c.update_state(force_full=bool(rng.random() < 0.1))
                 assert st["gates_total"] == sum(len(lv) for lv in model), sc
                 assert c.num_levels() == len(model), sc
+                segs = [c.segment_info(s) for s in range(c.num_segments())]
+                assert sum(si["nlevels"] for si in segs) == len(model), sc
             c.close()
 
         for sc in range(120):
