@@ -125,9 +125,15 @@ typedef struct {
  * Allocates host memory only.  *out receives the handle. */
 qt_status qt_create(int32_t n_qubits, int32_t dtype, int32_t log2_partition, qt_circuit** out);
 
-/* Free the circuit and all its host and device memory.  NULL is allowed. */
+/* Free the circuit and all its host and device memory.  NULL is allowed.
+ * Waits for the circuit's device work (and an asynchronous read in flight)
+ * first.  (No counterpart in the paper: its circuit is a C++ object,
+ * Listing 1, freed by its destructor.) */
 qt_status qt_destroy(qt_circuit* c);
 
+/* Number of levels (the paper's nets, Section III-B), and of gates over all
+ * levels, of the circuit as edited so far (pending edits included).
+ * QT_ERR_ARG if c or out is NULL. */
 qt_status qt_num_levels(const qt_circuit* c, int32_t* out);
 qt_status qt_num_gates(const qt_circuit* c, int64_t* out);
 
@@ -156,14 +162,26 @@ qt_status qt_replace_gate(qt_circuit* c, int32_t level, qt_gate_id id, const qt_
  * one run, each over the partitions its edits (or the dirty partitions
  * flowing in from earlier segments) can reach (Section III-E).
  * force_full = 1: every segment over every partition.  Both give the same
- * bits.  Blocks until the device work is done.  stats may be NULL.  On error
- * the previous state stays readable and the edits stay pending. */
+ * bits.  Blocks until the device work is done.  stats may be NULL.
+ * On error the edits stay pending (so reads return QT_ERR_STALE), and:
+ *   - an error raised before any device work is enqueued (QT_ERR_OOM from
+ *     mem_limit or a failed allocation, QT_ERR_ARG) leaves the device state
+ *     and every checkpoint of the last successful update untouched: undoing
+ *     the edits and updating again gives that state back bit for bit
+ *     without recomputing it, and otherwise the next update still runs
+ *     incrementally from those checkpoints;
+ *   - an error during the device work (QT_ERR_CUDA, QT_ERR_TIMEOUT) leaves
+ *     the checkpoints the update was rewriting in place unknown: the next
+ *     successful update re-simulates the whole circuit. */
 qt_status qt_update_state(qt_circuit* c, int32_t force_full, qt_update_stats* stats);
 
-/* Copy amplitudes [first, first + count) of the current state to host memory
- * (binary64 re/im pairs for QT_C128 and QT_C128_DF, binary32 pairs for
- * QT_C64).  QT_ERR_STALE while edits are pending; QT_ERR_RANGE if the range
- * exceeds 2^n. */
+/* Copy amplitudes [first, first + count) of the current state -- the
+ * alpha_b of Section II-A, b the index with qubit q at bit q -- to host
+ * memory (binary64 re/im pairs for QT_C128 and QT_C128_DF, binary32 pairs
+ * for QT_C64).  host_dst holds count x 16 bytes (8 for QT_C64) and stays the
+ * caller's.  Blocks until the copy is done.  QT_ERR_STALE while edits are
+ * pending or after a failed device update; QT_ERR_RANGE if the range exceeds
+ * 2^n; QT_ERR_ARG if host_dst is NULL with count > 0. */
 qt_status qt_read_amplitudes(const qt_circuit* c, uint64_t first, uint64_t count, void* host_dst);
 
 /* Same, into a device buffer of the caller (same element format). */
@@ -218,10 +236,12 @@ qt_status qt_probabilities(const qt_circuit* c, int32_t k, const int32_t* qubits
  * count: 1 <= count <= QT_NORM_STATIC_MAX_AMPS, else QT_ERR_RANGE.
  * Memory: the partial sums live in one file-scope device array of
  *   QT_NORM_STATIC_SCRATCH_BYTES bytes (1216 doubles), which every GPU that
- *   loads the library holds until the process exits.  The first call on a
- *   device looks up that array's device address (cudaGetSymbolAddress) with
- *   the device current; make that first call before any stream capture.
- *   The call never calls cudaMalloc, cudaFree or any allocating routine.
+ *   loads the library holds until the process exits.  Every call looks up
+ *   that array's address on the current device (cudaGetSymbolAddress, which
+ *   allocates nothing), so a context reset between calls does no harm; the
+ *   first call on a device may load the library's device code, so make it
+ *   before any stream capture.  The call never calls cudaMalloc, cudaFree or
+ *   any allocating routine.
  * Sharing: all calls share the one array, and it keeps the last call's
  *   contents (each call overwrites every partial sum it reads, so nothing
  *   needs clearing); two calls whose work overlaps on the GPU (on different
@@ -234,7 +254,12 @@ qt_status qt_probabilities(const qt_circuit* c, int32_t k, const int32_t* qubits
 qt_status qt_norm_static(const void* amps_device, uint64_t count, int32_t dtype, double* out_device,
                          void* cuda_stream);
 
-/* Options (value semantics):
+/* Tuning options.  The paper's one knob is the block size B (Section IV,
+ * "Impact of Block Size"), here log2_partition of qt_create; the checkpoint
+ * options choose how many of Section III-F's per-net state vectors are kept;
+ * the others have no counterpart in the paper.  QT_ERR_ARG for an unknown key
+ * or a value out of range; the circuit is then unchanged.
+ * Options (value semantics):
  *   "ckpt_interval"  levels per checkpoint segment (>= 1; default 4)
  *   "ckpt_budget"    > 0: bytes of device memory for the state and its
  *                    checkpoints (one state vector each); the interval is
@@ -262,7 +287,9 @@ qt_status qt_norm_static(const void* amps_device, uint64_t count, int32_t dtype,
 qt_status qt_set_option(qt_circuit* c, const char* key, int64_t value);
 
 /* Run the circuit's GPU work on `cuda_stream` (a cudaStream_t; NULL = the
- * library's own stream). */
+ * library's own stream).  The caller keeps ownership of the stream and must
+ * keep it alive while the circuit uses it.  (No counterpart in the paper,
+ * whose runtime is CPU-only.) */
 qt_status qt_set_stream(qt_circuit* c, void* cuda_stream);
 
 /* Introspection of the last qt_update_state (real or dry run), for tests and
@@ -274,8 +301,11 @@ qt_status qt_num_segments(const qt_circuit* c, int32_t* out);
 qt_status qt_segment_info(const qt_circuit* c, int32_t seg, int32_t* first_level, int32_t* nlevels,
                           int32_t* npasses, uint8_t* dirty_out, uint8_t* worklist_out);
 
-/* Message of the last failed call on c (or of the last failed qt_create when
- * c is NULL).  Valid until the next call on c. */
+/* Message of the last failed call on c (or of the last failed qt_create,
+ * qt_norm_static or batch call on this thread when c is NULL).  Valid until
+ * the next call on c.  (No counterpart in the paper: its modifiers throw a
+ * C++ exception on a conflicting gate, Section III-B; no exception crosses
+ * this ABI.) */
 const char* qt_last_error(const qt_circuit* c);
 
 /* Free the circuit's device memory (state, checkpoints, buffers) and keep

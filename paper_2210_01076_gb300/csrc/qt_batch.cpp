@@ -196,6 +196,12 @@ qt_status qt_batch_run(qt_batch* b, qt_batch_stats* stats) {
                 if (!dp.reg_kernel || dp.nwarp != 3 || dp.nreg < 2 || dp.nreg > 4)
                     return bfail(b, QT_ERR_ARG,
                                  "qt_batch_run: circuits need tiles of 2^10 to 2^12 amplitudes (10 or more qubits)");
+                // k_batch keeps a tile in at most 64 KB of shared memory and
+                // instantiates 2^12-amplitude tiles for 8-byte amplitudes only
+                if (dp.nreg == 4 && bytes_per_amp(dtype) != 8)
+                    return bfail(b, QT_ERR_ARG,
+                                 "qt_batch_run: 16-byte amplitudes need tiles of at most 2^11 amplitudes "
+                                 "(set tile_high <= 5)");
                 en.ntiles = 1u << dp.tpg_log2;
                 smem = std::max(smem, bytes_per_amp(dtype) << (dp.lt + dp.nh));
                 enc[c].push_back(std::move(en));
@@ -316,6 +322,7 @@ qt_status qt_batch_run(qt_batch* b, qt_batch_stats* stats) {
         }
         if ((e = cudaEventRecord(b->ev1, b->stream)) != cudaSuccess) return bfail(b, QT_ERR_CUDA, "event");
         if ((e = cudaStreamSynchronize(b->stream)) != cudaSuccess) return bfail(b, QT_ERR_CUDA, cudaGetErrorString(e));
+        if (*b->h_err == 2) return bfail(b, QT_ERR_ARG, "qt_batch_run: a tile shape the batch kernel does not support");
         if (*b->h_err) return bfail(b, QT_ERR_TIMEOUT, "qt_batch_run: a bounded wait between passes expired");
         if (stats) {
             std::memset(stats, 0, sizeof *stats);

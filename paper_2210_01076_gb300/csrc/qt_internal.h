@@ -284,6 +284,11 @@ int launch_read_convert(int dtype, void* dst, const void* state, uint64_t first,
 int launch_norm(int dtype, const void* state, uint64_t namps, double* partials, int npartials, double* out_dev,
                 void* stream);
 int norm_partials_needed(uint64_t namps);
+// Most partial sums launch_norm uses (8 per SM of a 152-SM GB300); the
+// no-allocation norm sizes its file-scope array to this.
+constexpr int kMaxNormPartials = 152 * 8;
+// Streaming multiprocessors of the current device (queried once per device).
+int device_sm_count();
 // Message for qt_last_error(NULL) on this thread.
 void set_thread_error(const std::string& msg);
 

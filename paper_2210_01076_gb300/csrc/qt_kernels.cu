@@ -34,6 +34,7 @@
 
 #include "qt_arith.cuh"
 #include "qt_internal.h"
+#include "qt_launch.cuh"
 
 namespace qt {
 
@@ -158,8 +159,8 @@ __device__ __forceinline__ void apply_op(typename A::amp_t* tile, uint32_t tb, c
 
 // One CTA per tile.  blockIdx.x = group index * 2^tpg_log2 + tile index.
 template <class A>
-__global__ void __launch_bounds__(kThreads) k_pass(typename A::amp_t* __restrict__ dst,
-                                                    const typename A::amp_t* __restrict__ src, const DevPass dp,
+__global__ void __launch_bounds__(kThreads) k_pass(typename A::amp_t* dst,
+                                                    const typename A::amp_t* src, const DevPass dp,
                                                     const DevOp* __restrict__ ops,
                                                     const uint32_t* __restrict__ worklist) {
     using amp_t = typename A::amp_t;
@@ -217,18 +218,16 @@ int launch_pass_t(void* dst, const void* src, const DevPass& dp, const DevOp* op
                   uint32_t ngroups, cudaStream_t st) {
     using amp_t = typename A::amp_t;
     const size_t smem = sizeof(amp_t) << (dp.lt + dp.nh);
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(k_pass<A>, cudaFuncAttributeMaxDynamicSharedMemorySize, 128 * 1024);
-        if (e != cudaSuccess) return int(e);
-        attr_set = true;
-    }
+    static DeviceOnce attr;
+    const int rc = attr.run([](int) {
+        return int(cudaFuncSetAttribute(k_pass<A>, cudaFuncAttributeMaxDynamicSharedMemorySize, 128 * 1024));
+    });
+    if (rc) return rc;
     const uint64_t nblocks = uint64_t(ngroups) << dp.tpg_log2;
     if (nblocks == 0) return 0;
     if (nblocks > 0x7fffffffull || smem > 128 * 1024) return int(cudaErrorInvalidConfiguration);
-    k_pass<A><<<unsigned(nblocks), kThreads, smem, st>>>(static_cast<amp_t*>(dst), static_cast<const amp_t*>(src),
-                                                          dp, ops, worklist);
-    return int(cudaGetLastError());
+    return launch_k(k_pass<A>, dim3(unsigned(nblocks)), dim3(kThreads), smem, st, static_cast<amp_t*>(dst),
+                    static_cast<const amp_t*>(src), dp, ops, worklist);
 }
 
 int launch_pass(int dtype, void* dst, const void* src, const DevPass& dp, const DevOp* ops, const uint32_t* worklist,
@@ -266,6 +265,18 @@ void encode_matrix(int dtype, const HostOp& op, DevOp* out) {
     }
 }
 
+// ---------------------------------------------------- device properties --
+int device_sm_count() {
+    static DeviceOnce once;
+    static int nsm[DeviceOnce::kMaxDevices];
+    const int rc = once.run(
+        [](int d) { return int(cudaDeviceGetAttribute(&nsm[d], cudaDevAttrMultiProcessorCount, d)); });
+    int dev = 0;
+    if (rc || cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= DeviceOnce::kMaxDevices || nsm[dev] < 1)
+        return 1;  // only sizes grid-stride loops; the launch itself reports the error
+    return nsm[dev];
+}
+
 // ------------------------------------------------------- state utilities --
 __global__ void k_copy_parts(uint4* __restrict__ dst, const uint4* __restrict__ src, const uint32_t* __restrict__ parts,
                              uint32_t nparts, uint32_t vec_per_part_log2) {
@@ -298,16 +309,14 @@ int launch_copy_parts(int dtype, void* dst, const void* src, int p, const uint32
     if (bytes >= 16) {
         const uint32_t vlog2 = uint32_t(p + (dtype == QT_C64 ? 3 : 4) - 4);
         const uint64_t total = uint64_t(nparts) << vlog2;
-        const unsigned grid = unsigned(std::min<uint64_t>((total + 255) / 256, 152 * 16));
-        k_copy_parts<<<grid, 256, 0, st>>>(static_cast<uint4*>(dst), static_cast<const uint4*>(src), parts, nparts,
-                                           vlog2);
-    } else {
-        const uint64_t total = uint64_t(nparts) * bytes;
-        const unsigned grid = unsigned(std::min<uint64_t>((total + 255) / 256, 152 * 16));
-        k_copy_bytes<<<grid, 256, 0, st>>>(static_cast<unsigned char*>(dst), static_cast<const unsigned char*>(src),
-                                           parts, nparts, uint32_t(bytes));
+        const unsigned grid = unsigned(std::min<uint64_t>((total + 255) / 256, uint64_t(device_sm_count()) * 16));
+        return launch_k(k_copy_parts, dim3(grid), dim3(256), 0, st, static_cast<uint4*>(dst),
+                        static_cast<const uint4*>(src), parts, nparts, vlog2);
     }
-    return int(cudaGetLastError());
+    const uint64_t total = uint64_t(nparts) * bytes;
+    const unsigned grid = unsigned(std::min<uint64_t>((total + 255) / 256, uint64_t(device_sm_count()) * 16));
+    return launch_k(k_copy_bytes, dim3(grid), dim3(256), 0, st, static_cast<unsigned char*>(dst),
+                    static_cast<const unsigned char*>(src), parts, nparts, uint32_t(bytes));
 }
 
 __global__ void k_set_first_one(void* state, int dtype) {
@@ -324,8 +333,7 @@ int launch_init_zero_state(int dtype, void* state, uint64_t namps, void* stream)
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     cudaError_t e = cudaMemsetAsync(state, 0, namps * bytes_per_amp(dtype), st);
     if (e != cudaSuccess) return int(e);
-    k_set_first_one<<<1, 1, 0, st>>>(state, dtype);
-    return int(cudaGetLastError());
+    return launch_k(k_set_first_one, dim3(1), dim3(1), 0, st, state, dtype);
 }
 
 // Float-float to binary64 for reading out QT_C128_DF states (not on the hot path).
@@ -341,9 +349,9 @@ int launch_read_convert(int dtype, void* dst, const void* state, uint64_t first,
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     if (count == 0) return 0;
     if (dtype == QT_C128_DF) {
-        const unsigned grid = unsigned(std::min<uint64_t>((count + 255) / 256, 152 * 16));
-        k_df_to_f64<<<grid, 256, 0, st>>>(static_cast<double2*>(dst), static_cast<const float4*>(state), first, count);
-        return int(cudaGetLastError());
+        const unsigned grid = unsigned(std::min<uint64_t>((count + 255) / 256, uint64_t(device_sm_count()) * 16));
+        return launch_k(k_df_to_f64, dim3(grid), dim3(256), 0, st, static_cast<double2*>(dst),
+                        static_cast<const float4*>(state), first, count);
     }
     const size_t b = bytes_per_amp(dtype);
     return int(cudaMemcpyAsync(dst, static_cast<const char*>(state) + first * b, count * b, cudaMemcpyDeviceToDevice,
@@ -419,19 +427,21 @@ __global__ void __launch_bounds__(kNormThreads) k_norm_final(const double* __res
 
 int norm_partials_needed(uint64_t namps) {
     const uint64_t blocks = (namps + kNormThreads - 1) / kNormThreads;
-    return int(std::min<uint64_t>(std::max<uint64_t>(blocks, 1), 152 * 8));
+    const uint64_t cap = std::min<uint64_t>(uint64_t(device_sm_count()) * 8, kMaxNormPartials);
+    return int(std::min<uint64_t>(std::max<uint64_t>(blocks, 1), cap));
 }
 
 int launch_norm(int dtype, const void* state, uint64_t namps, double* partials, int npartials, double* out_dev,
                 void* stream) {
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    switch (dtype) {
-        case QT_C128: k_norm_partial<QT_C128><<<npartials, kNormThreads, 0, st>>>(state, namps, partials); break;
-        case QT_C64: k_norm_partial<QT_C64><<<npartials, kNormThreads, 0, st>>>(state, namps, partials); break;
-        default: k_norm_partial<QT_C128_DF><<<npartials, kNormThreads, 0, st>>>(state, namps, partials); break;
-    }
-    k_norm_final<<<1, kNormThreads, 0, st>>>(partials, npartials, out_dev);
-    return int(cudaGetLastError());
+    if (npartials < 1 || npartials > kMaxNormPartials) return int(cudaErrorInvalidConfiguration);
+    void (*kp)(const void*, uint64_t, double*) = dtype == QT_C128 ? k_norm_partial<QT_C128>
+                                                 : dtype == QT_C64 ? k_norm_partial<QT_C64>
+                                                                   : k_norm_partial<QT_C128_DF>;
+    const int rc = launch_k(kp, dim3(npartials), dim3(kNormThreads), 0, st, state, namps, partials);
+    if (rc) return rc;
+    return launch_k(k_norm_final, dim3(1), dim3(kNormThreads), 0, st, static_cast<const double*>(partials),
+                    npartials, out_dev);
 }
 
 }  // namespace qt

@@ -10,14 +10,15 @@
 // caller already holds in device memory and keeps the partial sums in the
 // file-scope array below instead of allocating.
 //
-// The array is a host-side stand-in in host code, not a device address:
-// passing its name to a kernel from the host would fault or read the wrong
-// memory.  So on the first call on each device (with that device current)
-// cudaGetSymbolAddress resolves its device address once, and that address is
-// what the kernels get.
+// The array's name is a host-side stand-in in host code, not a device
+// address: passing it to a kernel from the host would fault or read the
+// wrong memory.  So every call asks cudaGetSymbolAddress, with the caller's
+// device current, for the array's device address on that device, and gives
+// the kernels that address.  The lookup allocates nothing; doing it on every
+// call (rather than caching it) keeps the address right across a context
+// reset (cudaDeviceReset) between calls.
 #include <cuda_runtime.h>
 
-#include <mutex>
 #include <string>
 
 #include "qt_internal.h"
@@ -25,33 +26,10 @@
 namespace qt {
 
 // One partial sum per reduction block; launch_norm never uses more blocks
-// than norm_partials_needed() returns, which is at most kNormStaticPartials.
-constexpr int kNormStaticPartials = 152 * 8;
+// than norm_partials_needed() returns, which is at most kMaxNormPartials.
+constexpr int kNormStaticPartials = kMaxNormPartials;
 static_assert(kNormStaticPartials * sizeof(double) == QT_NORM_STATIC_SCRATCH_BYTES, "documented scratch size");
 static __device__ __align__(256) double g_norm_scratch[kNormStaticPartials];
-
-namespace {
-constexpr int kMaxDevices = 64;
-std::mutex g_setup_mutex;
-double* g_scratch_ptr[kMaxDevices] = {nullptr};
-
-// Device address of g_norm_scratch on the current device (resolved once).
-cudaError_t scratch_address(double** out) {
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return e;
-    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
-    std::lock_guard<std::mutex> lock(g_setup_mutex);
-    if (!g_scratch_ptr[dev]) {
-        void* p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_norm_scratch);
-        if (e != cudaSuccess) return e;
-        g_scratch_ptr[dev] = static_cast<double*>(p);
-    }
-    *out = g_scratch_ptr[dev];
-    return cudaSuccess;
-}
-}  // namespace
 
 }  // namespace qt
 
@@ -76,15 +54,15 @@ extern "C" qt_status qt_norm_static(const void* amps_device, uint64_t count, int
         set_thread_error("qt_norm_static: more partial sums than the static scratch holds");
         return QT_ERR_RANGE;
     }
-    double* scratch = nullptr;
-    cudaError_t e = scratch_address(&scratch);
+    void* scratch = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&scratch, g_norm_scratch);
     if (e != cudaSuccess) {
         set_thread_error(std::string("qt_norm_static: cudaGetSymbolAddress failed: ") + cudaGetErrorString(e));
         return QT_ERR_CUDA;
     }
     // Every call writes all np partial sums before the final kernel reads
     // them, so nothing in the scratch needs clearing between calls.
-    const int rc = launch_norm(dtype, amps_device, count, scratch, np, out_device, cuda_stream);
+    const int rc = launch_norm(dtype, amps_device, count, static_cast<double*>(scratch), np, out_device, cuda_stream);
     if (rc) {
         set_thread_error(std::string("qt_norm_static: launch failed: ") + cudaGetErrorString(cudaError_t(rc)));
         return QT_ERR_CUDA;

@@ -26,6 +26,7 @@
 
 #include "qt_arith.cuh"
 #include "qt_internal.h"
+#include "qt_launch.cuh"
 
 // This file is compiled twice: as itself, with the kernels that have no
 // merged phase groups (RC_PH_GROUP) and the library's entry points, and from
@@ -487,8 +488,8 @@ constexpr int reg_min_blocks() {
 }
 
 template <class A, int RB, bool PG>
-__global__ void __launch_bounds__(256, reg_min_blocks<A, RB>()) k_pass_reg(typename A::amp_t* __restrict__ dst,
-                                                   const typename A::amp_t* __restrict__ src, const DevPass dp,
+__global__ void __launch_bounds__(256, reg_min_blocks<A, RB>()) k_pass_reg(typename A::amp_t* dst,
+                                                   const typename A::amp_t* src, const DevPass dp,
                                                    const DevOp* __restrict__ ops,
                                                    const uint32_t* __restrict__ worklist) {
     using amp_t = typename A::amp_t;
@@ -581,8 +582,8 @@ __device__ __forceinline__ void bulk_g2s(void* dst_smem, const void* src_gmem, u
 }
 
 template <class A, int RB, bool PG>
-__global__ void __launch_bounds__(256, (RB <= 3 ? 3 : 1)) k_pass_tma(typename A::amp_t* __restrict__ dst,
-                                                   const typename A::amp_t* __restrict__ src, const DevPass dp,
+__global__ void __launch_bounds__(256, (RB <= 3 ? 3 : 1)) k_pass_tma(typename A::amp_t* dst,
+                                                   const typename A::amp_t* src, const DevPass dp,
                                                    const DevOp* __restrict__ ops,
                                                    const uint32_t* __restrict__ worklist, uint32_t ntiles,
                                                    int* __restrict__ err) {
@@ -654,38 +655,29 @@ int launch_reg_t(void* dst, const void* src, const DevPass& dp, const DevOp* ops
     if (nblocks > 0x7fffffffull || tile_bytes > 64 * 1024 || dp.nreg != RB) return int(cudaErrorInvalidConfiguration);
     const bool tma = dp.tma && err != nullptr && (uint32_t(sizeof(amp_t)) << dp.lt) % 16 == 0;
     if (!tma) {
-        static bool attr_set = false;
-        if (!attr_set) {
-            cudaError_t e =
-                cudaFuncSetAttribute(k_pass_reg<A, RB, PG>, cudaFuncAttributeMaxDynamicSharedMemorySize, 128 * 1024);
-            if (e != cudaSuccess) return int(e);
-            attr_set = true;
-        }
-        k_pass_reg<A, RB, PG><<<unsigned(nblocks), threads, tile_bytes, st>>>(
-            static_cast<amp_t*>(dst), static_cast<const amp_t*>(src), dp, ops, worklist);
-        return int(cudaGetLastError());
+        static DeviceOnce attr;
+        const int rc = attr.run([](int) {
+            return int(cudaFuncSetAttribute(k_pass_reg<A, RB, PG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            128 * 1024));
+        });
+        if (rc) return rc;
+        return launch_k(k_pass_reg<A, RB, PG>, dim3(unsigned(nblocks)), dim3(threads), tile_bytes, st,
+                        static_cast<amp_t*>(dst), static_cast<const amp_t*>(src), dp, ops, worklist);
     }
-    static bool tattr_set = false;
-    static int nsm = 0;
-    if (!tattr_set) {
-        cudaError_t e =
-            cudaFuncSetAttribute(k_pass_tma<A, RB, PG>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
-        if (e != cudaSuccess) return int(e);
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-        tattr_set = true;
-    }
+    static DeviceOnce tattr;
+    int rc = tattr.run([](int) {
+        return int(
+            cudaFuncSetAttribute(k_pass_tma<A, RB, PG>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024));
+    });
+    if (rc) return rc;
     const size_t smem = 2 * tile_bytes;
     int per_sm = 0;
     cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pass_tma<A, RB, PG>, int(threads), smem);
     if (e != cudaSuccess) return int(e);
     if (per_sm < 1) per_sm = 1;
-    const uint64_t grid = std::min<uint64_t>(nblocks, uint64_t(nsm) * uint64_t(per_sm));
-    k_pass_tma<A, RB, PG><<<unsigned(grid), threads, smem, st>>>(static_cast<amp_t*>(dst),
-                                                             static_cast<const amp_t*>(src), dp, ops, worklist,
-                                                             uint32_t(nblocks), err);
-    return int(cudaGetLastError());
+    const uint64_t grid = std::min<uint64_t>(nblocks, uint64_t(device_sm_count()) * uint64_t(per_sm));
+    return launch_k(k_pass_tma<A, RB, PG>, dim3(unsigned(grid)), dim3(threads), smem, st, static_cast<amp_t*>(dst),
+                    static_cast<const amp_t*>(src), dp, ops, worklist, uint32_t(nblocks), err);
 }
 
 template <class A, bool PG>
@@ -808,14 +800,20 @@ __global__ void __launch_bounds__(256) k_batch(typename A::amp_t* __restrict__ a
         const DevPass dp = bp->dp;
         amp_t* state = arena + bp->state_off;
         const uint32_t t = item - bp->first_item;
+        // Tiles of 2^12 exist for 8-byte amplitudes only (the host rejects
+        // them for 16-byte ones); any other shape raises the error flag
+        // (2: unsupported tile) instead of leaving the tile undone.
+        bool done = true;
         switch (dp.nreg) {
             case 2: batch_tile<A, 2>(state, dp, t, ops, tile, choff); break;
             case 3: batch_tile<A, 3>(state, dp, t, ops, tile, choff); break;
-            case 4:  // tiles of 2^12 occur for complex64 only (16-byte amplitudes stop at 2^11)
+            case 4:
                 if constexpr (sizeof(amp_t) == 8) batch_tile<A, 4>(state, dp, t, ops, tile, choff);
+                else done = false;
                 break;
-            default: break;
+            default: done = false; break;
         }
+        if (!done && threadIdx.x == 0) atomicExch(err, 2);
         if (threadIdx.x == 0) {
             __threadfence();
             atomicAdd(counters + bp->counter, 1u);
@@ -843,36 +841,35 @@ int launch_batch_init(int dtype, void* arena, uint64_t arena_amps, const uint64_
     const int grid = (count + 255) / 256;
     if (grid == 0) return 0;
     switch (dtype) {
-        case QT_C128: k_batch_init<ArF64><<<grid, 256, 0, st>>>(static_cast<double2*>(arena), firsts, count); break;
-        case QT_C64: k_batch_init<ArF32><<<grid, 256, 0, st>>>(static_cast<float2*>(arena), firsts, count); break;
-        default: k_batch_init<ArDF><<<grid, 256, 0, st>>>(static_cast<float4*>(arena), firsts, count); break;
+        case QT_C128:
+            return launch_k(k_batch_init<ArF64>, dim3(grid), dim3(256), 0, st, static_cast<double2*>(arena), firsts,
+                            count);
+        case QT_C64:
+            return launch_k(k_batch_init<ArF32>, dim3(grid), dim3(256), 0, st, static_cast<float2*>(arena), firsts,
+                            count);
+        default:
+            return launch_k(k_batch_init<ArDF>, dim3(grid), dim3(256), 0, st, static_cast<float4*>(arena), firsts,
+                            count);
     }
-    return int(cudaGetLastError());
 }
 
 template <class A>
 int launch_batch_t(void* arena, const BatchPass* passes, int npasses, const DevOp* ops, uint32_t total_items,
                    uint32_t* head, uint32_t* counters, int* err, size_t smem, cudaStream_t st) {
-    static bool attr_set = false;
-    static int nsm = 0;
-    if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(k_batch<A>, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
-        if (e != cudaSuccess) return int(e);
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-        attr_set = true;
-    }
+    static DeviceOnce attr;
+    const int rc = attr.run([](int) {
+        return int(cudaFuncSetAttribute(k_batch<A>, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024));
+    });
+    if (rc) return rc;
     if (smem > 64 * 1024) return int(cudaErrorInvalidConfiguration);
     int per_sm = 0;
     cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch<A>, 256, smem);
     if (e != cudaSuccess) return int(e);
     if (per_sm < 1) per_sm = 1;
-    const uint64_t grid = std::min<uint64_t>(total_items, uint64_t(nsm) * uint64_t(per_sm));
+    const uint64_t grid = std::min<uint64_t>(total_items, uint64_t(device_sm_count()) * uint64_t(per_sm));
     if (grid == 0) return 0;
-    k_batch<A><<<unsigned(grid), 256, smem, st>>>(static_cast<typename A::amp_t*>(arena), passes, npasses, ops,
-                                                  total_items, head, counters, err);
-    return int(cudaGetLastError());
+    return launch_k(k_batch<A>, dim3(unsigned(grid)), dim3(256), smem, st, static_cast<typename A::amp_t*>(arena),
+                    passes, npasses, ops, total_items, head, counters, err);
 }
 
 int launch_batch(int dtype, void* arena, const BatchPass* passes, int npasses, const DevOp* ops,

@@ -11,6 +11,7 @@
 
 #include "qt_arith.cuh"
 #include "qt_internal.h"
+#include "qt_launch.cuh"
 
 namespace qt {
 
@@ -119,19 +120,17 @@ __global__ void __launch_bounds__(kRedThreads) k_prob_partial(const void* __rest
 
 template <int DA>
 int launch_fid_a(int db, const void* a, const void* b, uint64_t n, double* partials, int nblocks, cudaStream_t st) {
-    switch (db) {
-        case QT_C128: k_fid_partial<DA, QT_C128><<<nblocks, kRedThreads, 0, st>>>(a, b, n, partials); break;
-        case QT_C64: k_fid_partial<DA, QT_C64><<<nblocks, kRedThreads, 0, st>>>(a, b, n, partials); break;
-        default: k_fid_partial<DA, QT_C128_DF><<<nblocks, kRedThreads, 0, st>>>(a, b, n, partials); break;
-    }
-    return int(cudaGetLastError());
+    void (*k)(const void*, const void*, uint64_t, double*) = db == QT_C128  ? k_fid_partial<DA, QT_C128>
+                                                            : db == QT_C64 ? k_fid_partial<DA, QT_C64>
+                                                                           : k_fid_partial<DA, QT_C128_DF>;
+    return launch_k(k, dim3(nblocks), dim3(kRedThreads), 0, st, a, b, n, partials);
 }
 
 }  // namespace
 
 int reduce_blocks(uint64_t n) {
     const uint64_t blocks = (n + kRedThreads - 1) / kRedThreads;
-    return int(std::min<uint64_t>(std::max<uint64_t>(blocks, 1), 152 * 4));
+    return int(std::min<uint64_t>(std::max<uint64_t>(blocks, 1), uint64_t(device_sm_count()) * 4));
 }
 
 int launch_fidelity(int da, const void* a, int db, const void* b, uint64_t n, double* partials, int nblocks,
@@ -144,8 +143,7 @@ int launch_fidelity(int da, const void* a, int db, const void* b, uint64_t n, do
         default: rc = launch_fid_a<QT_C128_DF>(db, a, b, n, partials, nblocks, st); break;
     }
     if (rc) return rc;
-    k_sum_columns<<<1, 32, 0, st>>>(partials, nblocks, 4, out4);
-    return int(cudaGetLastError());
+    return launch_k(k_sum_columns, dim3(1), dim3(32), 0, st, static_cast<const double*>(partials), nblocks, 4, out4);
 }
 
 int launch_probabilities(int dtype, const void* s, uint64_t n, const QubitList& ql, double* partials, int nblocks,
@@ -153,15 +151,13 @@ int launch_probabilities(int dtype, const void* s, uint64_t n, const QubitList& 
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const int nb = 1 << ql.k;
     const size_t smem = sizeof(double) * nb;
-    switch (dtype) {
-        case QT_C128: k_prob_partial<QT_C128><<<nblocks, kRedThreads, smem, st>>>(s, n, ql, partials); break;
-        case QT_C64: k_prob_partial<QT_C64><<<nblocks, kRedThreads, smem, st>>>(s, n, ql, partials); break;
-        default: k_prob_partial<QT_C128_DF><<<nblocks, kRedThreads, smem, st>>>(s, n, ql, partials); break;
-    }
-    const int rc = int(cudaGetLastError());
+    void (*k)(const void*, uint64_t, QubitList, double*) = dtype == QT_C128  ? k_prob_partial<QT_C128>
+                                                           : dtype == QT_C64 ? k_prob_partial<QT_C64>
+                                                                             : k_prob_partial<QT_C128_DF>;
+    const int rc = launch_k(k, dim3(nblocks), dim3(kRedThreads), smem, st, s, n, ql, partials);
     if (rc) return rc;
-    k_sum_columns<<<(nb + 255) / 256, 256, 0, st>>>(partials, nblocks, nb, out);
-    return int(cudaGetLastError());
+    return launch_k(k_sum_columns, dim3((nb + 255) / 256), dim3(256), 0, st, static_cast<const double*>(partials),
+                    nblocks, nb, out);
 }
 
 }  // namespace qt

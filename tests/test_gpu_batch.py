@@ -130,3 +130,33 @@ def test_batch_passes_of_relabels_only(dtype):
     batch.close()
     for c in circs:
         c.close()
+
+
+@pytest.mark.parametrize("dtype", ["c128df", "c128", "c64"])
+def test_batch_tile_of_2_12_amplitudes(dtype):
+    """tile_high = 6 on 12+ qubits asks for tiles of 2^12 amplitudes.  The
+    batch kernel holds those only for 8-byte amplitudes (complex64); for
+    16-byte ones the run must fail with QT_ERR_ARG (not return a state with
+    tiles left undone), and complex64 must match the oracle."""
+    circs, levels = [], []
+    for k, n in enumerate((12, 13)):
+        lv = W.random_circuit(n, 90, seed=700 + k, p_multi=0.4)
+        c = B.Circuit(n, dtype, min(n, 10))
+        c.set_option("tile_high", 6)
+        c.load_levels(lv)
+        levels.append(lv)
+        circs.append(c)
+    batch = B.Batch(circs)
+    if dtype == "c64":
+        batch.run()
+        for k, c in enumerate(circs):
+            want = oracle.simulate(c.n, W.flatten(levels[k]))
+            assert max_err(batch.read_amplitudes(k), want) <= TOL[dtype], k
+    else:
+        with pytest.raises(B.QtError) as e:
+            batch.run()
+        assert e.value.status == B.QT_ERR_ARG
+        assert "2^11" in str(e.value) or "tile" in str(e.value)
+    batch.close()
+    for c in circs:
+        c.close()

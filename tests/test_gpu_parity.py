@@ -310,25 +310,70 @@ def test_norm_and_device_readout():
 
 
 def test_mem_limit_oom_keeps_state():
+    """An update refused for memory (QT_ERR_OOM, before any device work)
+    keeps the device state and checkpoints of the last successful update:
+    the edits stay pending (reads are stale); undoing them gives the old
+    state back bit for bit with no segment recomputed; with more memory the
+    same edit then updates incrementally, equal to a full re-simulation."""
     n = 14
     levels = W.random_circuit(n, 100, seed=1)
     c, ids = build_circuit(n, levels, "c128df", 8, ckpt_interval=1)
     c.update_state()
     before = c.read_amplitudes()
-    c.set_option("mem_limit", (1 << n) * 16 * 3)
+    held = c.device_bytes()
+    c.set_option("mem_limit", held)  # exactly the state and checkpoints held now
     c.insert_level(0)
-    c.insert_gate(0, W.make_gate("h", [0]))
+    gid = c.insert_gate(0, W.make_gate("h", [0]))  # one more level: one more checkpoint
     with pytest.raises(B.QtError) as e:
         c.update_state()
     assert e.value.status == B.QT_ERR_OOM
     with pytest.raises(B.QtError) as e:
         c.read_amplitudes()
     assert e.value.status == B.QT_ERR_STALE
+    # undo: the circuit is the last updated one again
+    c.remove_gate(0, gid)
+    c.remove_level(0)
+    st = c.update_state()
+    assert st["segments_run"] == 0 and st["launches"] == 0
+    assert np.array_equal(c.read_amplitudes(), before)
+    # redo with room for the new checkpoint: incremental from the kept checkpoints
     c.set_option("mem_limit", 0)
-    c.update_state()
+    c.insert_level(0)
+    c.insert_gate(0, W.make_gate("h", [0]))
+    st = c.update_state()
+    assert st["passes_run"] <= st["passes_total"]
     after = c.read_amplitudes()
+    c.update_state(force_full=True)
+    assert np.array_equal(after, c.read_amplitudes())
     want = oracle.simulate(n, [W.make_gate("h", [0])] + W.flatten(levels))
     assert max_err(after, want) <= 1e-12 and max_err(before, want) > 1e-3
+
+
+def test_timeout_mid_update_forces_a_full_resimulation():
+    """An update that fails during its device work (here the bounded wait of
+    the bulk-copy staged kernel expires: QT_ERR_TIMEOUT) has rewritten part of
+    its checkpoints: reads are stale, and the next update re-runs every pass
+    and gives the edited circuit's state."""
+    n, p = 12, 8
+    levels = W.random_circuit(n, 80, seed=9)
+    c, ids = build_circuit(n, levels, "c128df", p, ckpt_interval=2)
+    c.update_state()
+    c.set_option("tma", 1)
+    c.set_option("test_stall_staging", 1)
+    c.insert_level(len(levels))
+    c.insert_gate(len(levels), W.make_gate("rx", [3], [0.7]))
+    with pytest.raises(B.QtError) as e:
+        c.update_state()
+    assert e.value.status == B.QT_ERR_TIMEOUT
+    with pytest.raises(B.QtError) as e:
+        c.read_amplitudes()
+    assert e.value.status == B.QT_ERR_STALE
+    c.set_option("test_stall_staging", 0)
+    c.set_option("tma", 0)
+    st = c.update_state()
+    assert st["passes_run"] == st["passes_total"] and st["segments_run"] == st["segments_total"]
+    want = oracle.simulate(n, W.flatten(levels) + [W.make_gate("rx", [3], [0.7])])
+    assert max_err(c.read_amplitudes(), want) <= 1e-12
 
 
 def test_config2_full_size_parity_and_bit_identity():

@@ -7,7 +7,11 @@ fixed file-scope device array instead of a cudaMalloc'd buffer.
 
 The results are checked against qt_norm (the allocating entry point) on the
 same states, on two calls in a row (the second call reuses the array the
-first one left behind).  This file sorts last so that a run stopping at the
+first one left behind): bit for bit where both read the same bytes
+(complex128, complex64), within 1e-12 for the float-float layout the test
+rebuilds from the binary64 readout.  At n = 20 and 22 the reduction uses
+all 1216 partial sums the array holds, each block striding over several
+runs of the state.  This file sorts last so that a run stopping at the
 first failure has run every other test before it; it also passes alone."""
 import numpy as np
 import pytest
@@ -32,7 +36,7 @@ def _state(B, W, n, dtype):
 
 
 @pytest.mark.parametrize("dtype", ["c128", "c64", "c128df"])
-@pytest.mark.parametrize("n", [5, 17])
+@pytest.mark.parametrize("n", [5, 17, 20, 22])
 def test_norm_static_matches_qt_norm_twice(lib, dtype, n):
     import torch
     from paper_2210_01076_gb300 import workloads as W
@@ -57,14 +61,17 @@ def test_norm_static_matches_qt_norm_twice(lib, dtype, n):
             code = B.QT_C128_DF
     torch.cuda.synchronize()
     out = torch.full((1,), -1.0, dtype=torch.float64, device="cuda")
-    tol = 1e-12 if dtype != "c64" else 1e-6
     stream = torch.cuda.current_stream().cuda_stream
     for _ in range(2):
         out.fill_(-1.0)
         B.qt_norm_static(amps.data_ptr(), N, code, out.data_ptr(), stream)
         torch.cuda.synchronize()
         got = float(out.item())
-        assert abs(got - want) <= tol, (got, want)
+        if dtype == "c128df":
+            assert abs(got - want) <= 1e-12, (got, want)
+        else:
+            # the same kernels with the same grid on the same bytes
+            assert got == want, (got, want)
     c.close()
 
 
