@@ -299,6 +299,11 @@ def run_ours(args):
     for _ in range(3):
         fulls.append(c.update_state(force_full=True)["gpu_ms"])
     inc_lat = [s["gpu_ms"] for s in stats]
+    # per-round incremental efficiency: the round's time over the time a full
+    # re-simulation takes for the work left dirty (1 = the update costs
+    # exactly its dirty fraction of a full run; below 1 = cheaper)
+    full_p50 = pctl(fulls, 50)
+    eff = [s["gpu_ms"] / max((1.0 - s["clean_fraction"]) * full_p50, 1e-9) for s in stats]
 
     # ---- end to end through the public API with host buffers: edits in,
     # update, the whole state read back to pinned host memory, every step.
@@ -353,6 +358,10 @@ def run_ours(args):
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(levels, budget_s=args.cpu_seconds)
+    c.close()
+    configs = None
+    if rank == 0 and not args.no_configs:
+        configs = run_configs(args, levels)
 
     if rank == 0:
         line = {
@@ -375,6 +384,11 @@ def run_ours(args):
             "initial_full_sim_ms": full0["gpu_ms"],
             "clean_fraction_mean": float(np.mean([s["clean_fraction"] for s in stats])),
             "speedup_vs_full_p50": (pctl(fulls, 50) / pctl(inc_lat, 50)) if inc_lat else None,
+            "incremental_efficiency": {
+                "p50": pctl(eff, 50), "p99": pctl(eff, 99), "max": max(eff) if eff else None,
+                "definition": "per round: incremental update time / ((1 - clean fraction) x full re-simulation time)",
+                "rounds": [{"ms": s["gpu_ms"], "clean": s["clean_fraction"], "passes_run": s["passes_run"],
+                            "launches": s["launches"]} for s in stats]},
             "accuracy": accuracy,
             "gpu_launches": launches,
             "roofline": roofline_pair(achieved, peak, peak_kind, alu_ops, kern_ms, "c128df", traffic_per_launch,
@@ -388,8 +402,9 @@ def run_ours(args):
         }
         if cpu is not None:
             line["cpu_baseline"] = cpu
+        if configs is not None:
+            line["configs"] = configs
         print(json.dumps(line), flush=True)
-    c.close()
     if world > 1:
         dist.destroy_process_group()
 
@@ -439,6 +454,211 @@ def oracle_prefix_accuracy(B, W, n, p, dtype, keep, tol):
         c.close()
     return {"gates": len(gates), "max_abs_err_vs_fp64_oracle": err, "tolerance": tol,
             "note": "the oracle's prefix of the circuit (the CPU-baseline sample), whole state"}
+
+
+# ---------------------------------------------------------- other configs --
+# Compact fixed-setting runs of the other workloads, reported under "configs"
+# in the default line (each in seconds; no autotuning): the plain full
+# simulation (n = 12), the deep QFT-like circuit (n = 30, both dtypes), the
+# 256-circuit batch, a short served stream, and IEEE binary64 on the
+# incremental workload's circuit.  A block that fails records its error and
+# leaves the headline line intact.
+
+def _guard(fn, *a, **k):
+    try:
+        return fn(*a, **k)
+    except Exception as ex:  # the headline must survive a failing side block
+        return {"error": f"{type(ex).__name__}: {ex}"}
+
+
+def config1_block(B, W):
+    """n = 12, 200 gates uniform over the 14 kinds, partitions of 2^8, one
+    segment: full-simulation latency (the state is 64 KiB: L2-resident, bound
+    by launches, not HBM), float-float and IEEE binary64, whole state against
+    the FP64 oracle."""
+    import oracle
+    n, ng, p = 12, 200, 8
+    levels = W.random_circuit(n, ng, seed=SEED, p_multi=None)
+    want = oracle.simulate(n, W.flatten(levels))
+    out = {"workload": f"plain full simulation n={n}, {ng} gates (14 kinds uniform), partitions 2^{p}"}
+    for dt in ("c128df", "c128"):
+        c = B.Circuit(n, dt, p)
+        c.set_option("ckpt_interval", 1 << 20)
+        c.load_levels(levels)
+        c.update_state()
+        sts = [c.update_state(force_full=True) for _ in range(30)]
+        ms = [x["gpu_ms"] for x in sts]
+        err = float(np.max(np.abs(c.read_amplitudes() - want)))
+        c.close()
+        out[dt] = {"full_sim_ms": {"p50": pctl(ms, 50), "p99": pctl(ms, 99)},
+                   "host_ms_p50": pctl([x["host_ms"] for x in sts], 50),
+                   "amp_updates_per_s": ng * (1 << n) / (pctl(ms, 50) * 1e-3),
+                   "passes": sts[-1]["passes_total"], "launches": sts[-1]["launches"],
+                   "accuracy": {"max_abs_err_vs_fp64_oracle": err, "tolerance": 1e-12, "whole_state": True}}
+    return out
+
+
+def _tail_edits(B, W, c, ids, levels, count, seed):
+    rng = np.random.default_rng(seed)
+    inc = []
+    while len(inc) < count:
+        e = W.tail_edit(rng, levels)
+        if e is None:
+            continue
+        lvl, k, ng = e
+        ids[lvl][k] = c.replace_gate(lvl, ids[lvl][k], ng)
+        levels[lvl][k] = ng
+        inc.append(c.update_state())
+    return inc
+
+
+def config3_block(B, W, peak, peak_kind):
+    """n = 30, 2000 gates of QFT-like ladders and U3/CZ layers, partitions of
+    2^18, fusion width 5 (the autotuner's choice), checkpoints sized from a
+    device budget; a full simulation and 5 single-gate edits in the last 10 %
+    of the levels, complex64 and float-float complex128.  Accuracy: the
+    complex64 result against the float-float one over all 2^30 amplitudes
+    (on the device); the float-float path's own error against the FP64
+    oracle is measured on the incremental workload's whole state."""
+    n, p, ng = 30, 18, 2000
+    base = W.qft_like_circuit(n, ng, seed=7)
+    out = {"workload": f"QFT-like n={n}, {ng} gates, partitions 2^{p}, fusion width 5, 5 tail edits"}
+    # unfused HBM view first (its circuits are freed before the fused ones)
+    for dt in ("c64", "c128df"):
+        out.setdefault(dt, {})["unfused"] = deep30_unfused(B, W, n, p, dt, base, peak, 64)
+    kept = {}
+    try:
+        for dt, budget_gb in (("c64", 64.0), ("c128df", 120.0)):
+            levels = [list(x) for x in base]
+            c = B.Circuit(n, dt, p)
+            c.set_option("tile_high", 5)
+            c.set_option("ckpt_budget", int(budget_gb * 1e9))
+            ids = c.load_levels(levels)
+            c.update_state()
+            c.set_option("kernel_timing", 1)
+            full = c.update_state(force_full=True)
+            c.set_option("kernel_timing", 0)
+            inc = _tail_edits(B, W, c, ids, levels, 5, seed=11)
+            kept[dt] = c
+            bpa = 8 if dt == "c64" else 16
+            kb, km = full["pass_kernel_bytes"], full["pass_kernel_ms"]
+            achieved = kb / (km * 1e-3) / 1e9 if km > 0 else None
+            out[dt].update({
+                "full_sim_ms": full["gpu_ms"], "amp_updates_per_s": full["amp_updates"] / (full["gpu_ms"] * 1e-3),
+                "hbm_gbs": full["hbm_bytes"] / (full["gpu_ms"] * 1e-3) / 1e9,
+                "segments": full["segments_total"], "passes": full["passes_total"], "ckpt_budget_gb": budget_gb,
+                "incremental_ms": {"p50": pctl([x["gpu_ms"] for x in inc], 50),
+                                   "p99": pctl([x["gpu_ms"] for x in inc], 99)},
+                "clean_fraction_mean": float(np.mean([x["clean_fraction"] for x in inc])),
+                "roofline": roofline_pair(achieved, peak, peak_kind, full["pass_kernel_alu_ops"], km, dt, None,
+                                          full["pass_kernel_launches"], f"{2 * bpa} B per amplitude per pass")})
+        c64, df = kept["c64"], kept["c128df"]
+        out["c64"]["accuracy"] = {
+            "max_abs_vs_c128df_whole_state": c64.max_abs_diff(df), "fidelity_vs_c128df": c64.fidelity(df),
+            "norm": c64.norm(), "tolerance": {"max_abs": 1e-5, "fidelity": 1 - 1e-6},
+            "note": "both after the same full simulation and 5 tail edits; the float-float reference is within "
+                    "1e-12 of the FP64 oracle"}
+        out["c128df"]["accuracy"] = {"norm": df.norm(), "tolerance": 1e-12,
+                                     "note": "float-float error against the FP64 oracle: the headline's whole-state "
+                                             "check and --workload deep30 --deep-oracle-full"}
+    finally:
+        for c in kept.values():
+            c.close()
+    return out
+
+
+def config4_block(B, W):
+    """256 complex64 circuits of 10-20 qubits and depths 50-400, one
+    persistent launch, fusion width 5, then 3 rounds of one RZ/RY angle edit
+    per circuit replayed from the captured CUDA graph; the smallest and the
+    largest circuit against the oracle after the last round."""
+    import oracle
+    rng = np.random.default_rng(404)
+    circs, levels, ids = [], [], []
+    for n, lvls in W.batch_circuits(256, rng):
+        c = B.Circuit(n, "c64", min(n, 16))
+        c.set_option("tile_high", 5)
+        ids.append(c.load_levels(lvls))
+        levels.append([list(x) for x in lvls])
+        circs.append(c)
+    batch = B.Batch(circs)
+    try:
+        first = batch.run()
+        capture = batch.run()
+        rounds = []
+        for _ in range(3):
+            for k, c in enumerate(circs):
+                e = W.rotation_edit(rng, levels[k])
+                if e is None:
+                    continue
+                l, j, ng = e
+                ids[k][l][j] = c.replace_gate(l, ids[k][l][j], ng)
+                levels[k][l][j] = ng
+            rounds.append(batch.run())
+        acc = []
+        for k in (int(np.argmin([c.n for c in circs])), int(np.argmax([c.n for c in circs]))):
+            got = batch.read_amplitudes(k).astype(np.complex128)
+            want = oracle.simulate(circs[k].n, W.flatten(levels[k]), nthreads=oracle.max_threads())
+            acc.append({"qubits": circs[k].n, "gates": len(W.flatten(levels[k])),
+                        "max_abs_err_vs_fp64_oracle": float(np.max(np.abs(got - want))),
+                        "fidelity": float(abs(np.vdot(want, got)) ** 2 / np.vdot(got, got).real)})
+        ms = [r["gpu_ms"] for r in rounds]
+        return {"workload": "batch of 256 complex64 circuits, 10-20 qubits, depth 50-400, fusion width 5",
+                "round_ms": {"p50": pctl(ms, 50), "p99": pctl(ms, 99)}, "first_run_ms": first["gpu_ms"],
+                "capture_run_ms": capture["gpu_ms"], "graph_replays": int(sum(r["graph_replayed"] for r in rounds)),
+                "amp_updates_per_s": rounds[-1]["amp_updates"] / (np.median(ms) * 1e-3),
+                "tiles_per_launch": rounds[-1]["tiles"], "passes": rounds[-1]["passes"],
+                "accuracy": {"circuits": acc, "tolerance": {"max_abs": 1e-5, "fidelity": 1 - 1e-6},
+                             "whole_state": True}}
+    finally:
+        batch.close()
+        for c in circs:
+            c.close()
+
+
+def ieee_c128_block(B, W, levels):
+    """IEEE binary64 (QT_C128) on the incremental workload's circuit (n = 24,
+    1000 gates, partitions 2^16, checkpoints every 4 levels): full
+    re-simulation time against the float-float path of the same circuit,
+    with the fused pass against the binary64 FMA roof."""
+    out = {"workload": "incremental workload's circuit, full re-simulation"}
+    for dt in ("c128", "c128df"):
+        c = B.Circuit(N_QUBITS, dt, LOG2_PART)
+        c.set_option("ckpt_interval", CKPT)
+        c.load_levels(levels)
+        c.update_state()
+        c.set_option("kernel_timing", 1)
+        sts = [c.update_state(force_full=True) for _ in range(3)]
+        c.close()
+        st = min(sts, key=lambda x: x["gpu_ms"])
+        km = st["pass_kernel_ms"]
+        alu = st["pass_kernel_alu_ops"] / (km * 1e-3) / 1e12 if km > 0 else None
+        peak = FP64_PEAK_TOPS if dt == "c128" else FP32_PEAK_TOPS
+        out[dt] = {"full_sim_ms": st["gpu_ms"], "amp_updates_per_s": st["amp_updates"] / (st["gpu_ms"] * 1e-3),
+                   "pass_kernel_ms": km,
+                   "hbm_gbs_kernel": st["pass_kernel_bytes"] / (km * 1e-3) / 1e9 if km > 0 else None,
+                   "alu": {"achieved": alu, "peak": peak, "frac": alu / peak if alu else None,
+                           "unit": "T binary64 FMA-class ops/s" if dt == "c128" else "T binary32 ops/s"}}
+    out["float_float_speedup"] = out["c128"]["full_sim_ms"] / out["c128df"]["full_sim_ms"]
+    return out
+
+
+def run_configs(args, levels):
+    from paper_2210_01076_gb300 import binding as B
+    from paper_2210_01076_gb300 import workloads as W
+    peak, peak_kind = measured_peak()
+    t0 = time.perf_counter()
+    out = {}
+    out["plain_full_n12"] = _guard(config1_block, B, W)
+    out["ieee_binary64_n24"] = _guard(ieee_c128_block, B, W, levels)
+    out["deep_qft_n30"] = _guard(config3_block, B, W, peak, peak_kind)
+    out["batch256"] = _guard(config4_block, B, W)
+    if args.configs_serve:
+        sargs = argparse.Namespace(**vars(args))
+        sargs.serve_seconds, sargs.serve_burst, sargs.serve_check = 1.0, 100, 0
+        out["serve64"] = _guard(run_serve, sargs, emit=False)
+    out["wall_s"] = time.perf_counter() - t0
+    return out
 
 
 # ------------------------------------------------------------- reference --
@@ -501,6 +721,7 @@ def run_deep30(args):
         levels[lvl][k] = ng
         inc.append(c.update_state())
     norm = c.norm()
+    accuracy_full = deep30_whole_state_accuracy(B, W, c, n, p, dtype, levels, args.deep_oracle_full)
     peak, peak_kind = measured_peak()
     kb, km = full["pass_kernel_bytes"], full["pass_kernel_ms"]
     achieved = kb / (km * 1e-3) / 1e9 if km > 0 else None
@@ -527,6 +748,7 @@ def run_deep30(args):
                                    "p99": pctl([s["gpu_ms"] for s in inc], 99)},
         "clean_fraction_mean": float(np.mean([s["clean_fraction"] for s in inc])) if inc else None,
         "norm": norm,
+        "accuracy_whole_state": accuracy_full,
         "roofline": roofline_pair(achieved, peak, peak_kind, full["pass_kernel_alu_ops"], km, dtype, traffic_per_launch,
                                   full["pass_kernel_launches"], f"{2 * bpa} B per amplitude per pass"),
     }
@@ -538,6 +760,44 @@ def run_deep30(args):
         line["accuracy"] = oracle_prefix_accuracy(B, W, n, p, dtype, keep, 1e-5 if dtype == "c64" else 1e-12)
         keep.clear()
     print(json.dumps(line), flush=True)
+
+
+def deep30_whole_state_accuracy(B, W, c, n, p, dtype, levels, with_oracle):
+    """The final state (after the full simulation and the tail edits) over
+    all 2^n amplitudes: a complex64 result against a float-float run of the
+    same gates (on the device); with `with_oracle`, the result against the
+    FP64 oracle's full simulation of the same gates on the host cores
+    (2000 gates on 2^30 amplitudes: minutes on 16 cores, 16 GiB)."""
+    out = {}
+    if dtype == "c64":
+        ref = B.Circuit(n, "c128df", p)
+        try:
+            ref.set_option("ckpt_interval", 1 << 20)
+            ref.load_levels(levels)
+            ref.update_state()
+            out["vs_c128df"] = {"max_abs": c.max_abs_diff(ref), "fidelity": c.fidelity(ref),
+                                "tolerance": {"max_abs": 1e-5, "fidelity": 1 - 1e-6}}
+        finally:
+            ref.close()
+    if with_oracle:
+        import oracle
+        t0 = time.perf_counter()
+        want = oracle.simulate(n, W.flatten(levels), nthreads=oracle.max_threads())
+        t_or = time.perf_counter() - t0
+        err, dot, na, chunk = 0.0, 0j, 0.0, 1 << 24
+        for first in range(0, 1 << n, chunk):
+            cnt = min(chunk, (1 << n) - first)
+            a = c.read_amplitudes(first, cnt).astype(np.complex128)
+            w = want[first:first + cnt]
+            err = max(err, float(np.max(np.abs(a - w))))
+            dot += np.vdot(w, a)
+            na += float(np.vdot(a, a).real)
+        out["vs_fp64_oracle"] = {"max_abs": err, "fidelity": float(abs(dot) ** 2 / na),
+                                 "tolerance": 1e-5 if dtype == "c64" else 1e-12,
+                                 "oracle_s": t_or, "oracle_threads": oracle.max_threads(),
+                                 "gates": len(W.flatten(levels))}
+        del want
+    return out or None
 
 
 def deep30_unfused(B, W, n, p, dtype, levels, peak, ngates):
@@ -563,7 +823,7 @@ def deep30_unfused(B, W, n, p, dtype, levels, peak, ngates):
             "amp_updates_per_s": st["amp_updates"] / (st["gpu_ms"] * 1e-3)}
 
 
-def run_serve(args):
+def run_serve(args, emit=True):
     """Served request stream: 64 resident circuits of 16-28 qubits (complex64,
     300-1500 random gates), requests of 1-5 edits + an incremental update
     arriving as a Poisson stream, device memory admitted against a 150 GB
@@ -649,9 +909,14 @@ def run_serve(args):
         wall = time.perf_counter() - start
         lat = [r["latency_ms"] for r in results]
         amp = sum(r["stats"]["amp_updates"] for r in results)
+        # device time of every request's update (events on its circuit's
+        # stream) summed over the window: above the wall time only if
+        # requests' work overlapped on the device
+        dev_ms = sum(max(r["stats"]["gpu_ms"], 0.0) for r in results)
         return {"offered_req_s": rate, "window_s": seconds, "requests": len(results), "wall_s": wall,
                 "throughput_req_s": len(results) / wall, "amp_updates_per_s": amp / wall,
                 "latency_ms": {"p50": pctl(lat, 50), "p99": pctl(lat, 99)},
+                "device_ms_sum": dev_ms, "overlap_factor": dev_ms / (wall * 1e3),
                 "queue_ms_p50": pctl([r["queue_ms"] for r in results], 50),
                 "service_ms_p50": pctl([r["service_ms"] for r in results], 50),
                 "errors": sum(1 for r in results if r["status"] != 0)}
@@ -661,21 +926,54 @@ def run_serve(args):
     tb = time.perf_counter()
     tickets = [srv.submit(slots[c], ops) for c, ops in burst]
     res = [srv.wait(t) for t in tickets]
-    cap = len(res) / (time.perf_counter() - tb)
+    burst_wall = time.perf_counter() - tb
+    cap = len(res) / burst_wall
+    burst_dev_ms = sum(max(r["stats"]["gpu_ms"], 0.0) for r in res)
     at_2k = open_loop(2000.0, args.serve_seconds)
     at_70 = open_loop(0.7 * cap, args.serve_seconds)
     info = srv.info()
     srv.close()
-    accuracy = serve_accuracy(B, circs, mirrors, ns, args.serve_check)
+    accuracy = serve_accuracy(B, circs, mirrors, ns, args.serve_check) if args.serve_check > 0 else None
+    oracle_acc = serve_oracle_accuracy(B, circs, mirrors, ns, max_qubits=args.serve_oracle_max_n)
     line = {"metric": "served requests", "workload": "serve64", "dtype": "c64 (fp32)",
             "config": {"circuits": ncirc, "qubits": "16-28", "gates": "300-1500", "edits_per_request": "1-5",
                        "workers": args.serve_workers, "hbm_budget_gb": args.serve_budget_gb},
-            "warmup_full_sims_s": warm_s, "capacity_req_s": cap, "at_offered_2000": at_2k,
+            "warmup_full_sims_s": warm_s, "capacity_req_s": cap,
+            "capacity_burst": {"requests": len(res), "wall_s": burst_wall, "device_ms_sum": burst_dev_ms,
+                               "overlap_factor": burst_dev_ms / (burst_wall * 1e3),
+                               "device_ms_per_request_p50": pctl([r["stats"]["gpu_ms"] for r in res], 50),
+                               "device_ms_per_request_mean": burst_dev_ms / max(len(res), 1)},
+            "at_offered_2000": at_2k,
             "at_70pct_capacity": at_70, "evictions": info["evictions"],
-            "resident_gb": info["resident_bytes"] / 1e9, "accuracy_vs_plain_c128": accuracy}
-    print(json.dumps(line), flush=True)
+            "resident_gb": info["resident_bytes"] / 1e9, "accuracy_vs_plain_c128": accuracy,
+            "accuracy_vs_fp64_oracle": oracle_acc}
     for c in circs:
         c.close()
+    if emit:
+        print(json.dumps(line), flush=True)
+    return line
+
+
+def serve_oracle_accuracy(B, circs, mirrors, ns, max_qubits=22):
+    """The served complex64 states of every circuit of at most `max_qubits`
+    qubits, after all requests, against the FP64 oracle over the whole state
+    (the oracle takes seconds per circuit up to 22 qubits on the host cores)."""
+    import oracle
+    from paper_2210_01076_gb300 import workloads as W
+    picks = sorted((c for c in range(len(circs)) if ns[c] <= max_qubits), key=lambda c: -ns[c])[:3]
+    per, worst_err, worst_fid = [], 0.0, 1.0
+    for c in picks:
+        circs[c].update_state()  # re-simulates a circuit the server evicted (the same bits)
+        got = circs[c].read_amplitudes().astype(np.complex128)
+        want = oracle.simulate(ns[c], W.flatten(mirrors[c]), nthreads=oracle.max_threads())
+        err = float(np.max(np.abs(got - want)))
+        fid = float(abs(np.vdot(want, got)) ** 2 / (np.vdot(got, got).real * np.vdot(want, want).real))
+        per.append({"qubits": ns[c], "gates": int(sum(len(lv) for lv in mirrors[c])), "max_abs_err": err,
+                    "fidelity": fid})
+        worst_err, worst_fid = max(worst_err, err), min(worst_fid, fid)
+        circs[c].release_device()
+    return {"circuits_checked": len(per), "max_abs_err": worst_err, "min_fidelity": worst_fid,
+            "tolerance": {"max_abs": 1e-5, "fidelity": 1 - 1e-6}, "per_circuit": per, "whole_state": True}
 
 
 def serve_accuracy(B, circs, mirrors, ns, count):
@@ -824,6 +1122,10 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-oracle-check", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg (profiling runs)")
+    ap.add_argument("--no-configs", action="store_true", help="skip the other configurations' compact runs")
+    ap.add_argument("--configs-serve", type=int, default=1, help="include the short served stream in 'configs'")
+    ap.add_argument("--serve-oracle-max-n", type=int, default=22,
+                    help="serve: circuits up to this many qubits are checked against the FP64 oracle")
     ap.add_argument("--n-qubits", type=int, default=N_QUBITS, help="smaller cases for profiling only")
     ap.add_argument("--ckpt", type=int, default=CKPT, help="levels per checkpoint segment")
     ap.add_argument("--option", action="append", default=[], help="extra qt_set_option key=value")
@@ -846,6 +1148,8 @@ def main():
     ap.add_argument("--deep-oracle-s", type=float, default=15.0,
                     help="deep30: seconds of FP64 oracle on the host cores (a prefix of the circuit); 0 = skip")
     ap.add_argument("--deep-n", type=int, default=30, help="deep30: qubits (smaller cases for profiling only)")
+    ap.add_argument("--deep-oracle-full", type=int, default=0,
+                    help="deep30: 1 = also the FP64 oracle's whole 2000-gate simulation (minutes on the host cores)")
     ap.add_argument("--deep-unfused-gates", type=int, default=64,
                     help="deep30: gates timed one per pass (fusion off) for the HBM-bound view; 0 = skip")
     args = ap.parse_args()

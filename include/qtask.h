@@ -213,6 +213,16 @@ qt_status qt_norm(const qt_circuit* c, double* out);
  * tree).  Runs on a's stream after waiting for b's. */
 qt_status qt_fidelity(const qt_circuit* a, const qt_circuit* b, double* out);
 
+/* Largest amplitude difference max_b |alpha_b - beta_b| between the current
+ * states of two circuits with the same qubit count (any dtypes), computed
+ * in binary64 on the device (each amplitude converted to binary64: binary32
+ * exactly, float-float as hi + lo).  Against a complex128 run of the same
+ * gates it measures the complex64 rounding error per amplitude, the
+ * quantity the max-abs tolerance bounds.  Both states must be readable.
+ * Runs on a's stream after waiting for b's.  (No counterpart in the paper,
+ * which states no precision.) */
+qt_status qt_max_abs_diff(const qt_circuit* a, const qt_circuit* b, double* out);
+
 /* Marginal probabilities of the k <= 10 qubits qubits[0..k-1] in the current
  * state: out[v] (2^k doubles, host memory) = sum of |alpha_b|^2 over the
  * indices b whose bit qubits[j] equals bit j of v (squared amplitudes are

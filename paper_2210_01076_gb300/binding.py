@@ -45,7 +45,7 @@ class qt_update_stats(ctypes.Structure):
 
 EXPORTED = ["qt_create", "qt_destroy", "qt_num_levels", "qt_num_gates", "qt_insert_level", "qt_remove_level",
             "qt_insert_gate", "qt_remove_gate", "qt_replace_gate", "qt_update_state", "qt_read_amplitudes",
-            "qt_read_amplitudes_device", "qt_read_amplitudes_async", "qt_read_wait", "qt_norm", "qt_norm_static", "qt_fidelity", "qt_probabilities",
+            "qt_read_amplitudes_device", "qt_read_amplitudes_async", "qt_read_wait", "qt_norm", "qt_norm_static", "qt_fidelity", "qt_max_abs_diff", "qt_probabilities",
             "qt_set_option", "qt_set_stream", "qt_num_segments", "qt_segment_info", "qt_last_error",
             "qt_batch_create", "qt_batch_run", "qt_batch_read_amplitudes", "qt_batch_destroy",
             "qt_batch_last_error",
@@ -142,6 +142,7 @@ def load(path: str = LIB_PATH):
         "qt_norm": [P, ctypes.POINTER(ctypes.c_double)],
         "qt_norm_static": [P, u64, i32, P, P],
         "qt_fidelity": [P, P, ctypes.POINTER(ctypes.c_double)],
+        "qt_max_abs_diff": [P, P, ctypes.POINTER(ctypes.c_double)],
         "qt_probabilities": [P, i32, ctypes.POINTER(i32), ctypes.POINTER(ctypes.c_double)],
         "qt_set_option": [P, ctypes.c_char_p, i64],
         "qt_set_stream": [P, P],
@@ -289,6 +290,12 @@ def qt_fidelity(ha, hb) -> float:
     return v.value
 
 
+def qt_max_abs_diff(ha, hb) -> float:
+    v = ctypes.c_double()
+    _check(ha, load().qt_max_abs_diff(ha, hb, ctypes.byref(v)))
+    return v.value
+
+
 def qt_probabilities(h, qubits) -> np.ndarray:
     k = len(qubits)
     q = (ctypes.c_int32 * max(k, 1))(*[int(x) for x in qubits])
@@ -430,6 +437,9 @@ class Circuit:
 
     def fidelity(self, other: "Circuit") -> float:
         return qt_fidelity(self.h, other.h)
+
+    def max_abs_diff(self, other: "Circuit") -> float:
+        return qt_max_abs_diff(self.h, other.h)
 
     def probabilities(self, qubits) -> np.ndarray:
         return qt_probabilities(self.h, qubits)

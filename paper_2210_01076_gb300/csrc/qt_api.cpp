@@ -23,6 +23,7 @@
 
 #include <algorithm>
 #include <chrono>
+#include <cmath>
 #include <cstring>
 #include <new>
 #include <stdexcept>
@@ -1029,6 +1030,35 @@ qt_status qt_fidelity(const qt_circuit* ca, const qt_circuit* cb, double* out) {
     if ((e = cudaStreamSynchronize(a->stream)) != cudaSuccess) return cuda_fail(a, e, "fidelity");
     if (!(h[2] > 0.0) || !(h[3] > 0.0)) return fail(a, QT_ERR_ARG, "a state has zero norm");
     *out = (h[0] * h[0] + h[1] * h[1]) / (h[2] * h[3]);
+    return QT_OK;
+    QT_GUARD_END(a)
+}
+
+qt_status qt_max_abs_diff(const qt_circuit* ca, const qt_circuit* cb, double* out) {
+    qt_circuit* a = const_cast<qt_circuit*>(ca);
+    qt_circuit* b = const_cast<qt_circuit*>(cb);
+    if (!a) return QT_ERR_ARG;
+    if (!b || !out) return fail(a, QT_ERR_ARG, "b and out must not be NULL");
+    QT_GUARD_BEGIN
+    if (a->n != b->n) return fail(a, QT_ERR_ARG, "the two circuits have different qubit counts");
+    qt_status rs = check_readable(a);
+    if (rs != QT_OK) return rs;
+    rs = check_readable(b);
+    if (rs != QT_OK) return fail(a, rs, std::string("second circuit: ") + b->err);
+    cudaError_t e;
+    if (b->stream != a->stream && (e = cudaStreamSynchronize(b->stream)) != cudaSuccess)
+        return cuda_fail(a, e, "max_abs_diff");
+    const int nb = reduce_blocks(a->namps());
+    if ((rs = grow_device(a, &a->d_red, &a->d_red_cap, size_t(nb))) != QT_OK) return rs;
+    if ((rs = grow_device(a, &a->d_red_out, &a->d_red_out_cap, 4)) != QT_OK) return rs;
+    int rc = launch_max_sq_diff(a->dtype, final_state(a), b->dtype, final_state(b), a->namps(), a->d_red, nb,
+                                a->d_red_out, a->stream);
+    if (rc) return cuda_fail(a, rc, "max_abs_diff");
+    double h = 0.0;
+    if ((e = cudaMemcpyAsync(&h, a->d_red_out, sizeof h, cudaMemcpyDeviceToHost, a->stream)) != cudaSuccess)
+        return cuda_fail(a, e, "max_abs_diff");
+    if ((e = cudaStreamSynchronize(a->stream)) != cudaSuccess) return cuda_fail(a, e, "max_abs_diff");
+    *out = std::sqrt(h);
     return QT_OK;
     QT_GUARD_END(a)
 }

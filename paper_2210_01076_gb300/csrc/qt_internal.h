@@ -333,6 +333,10 @@ int reduce_blocks(uint64_t n);
 // out4 (device) receives Re<a|b>, Im<a|b>, <a|a>, <b|b>; partials: 4 per block.
 int launch_fidelity(int da, const void* a, int db, const void* b, uint64_t n, double* partials, int nblocks,
                     double* out4, void* stream);
+// out (device, one double) receives max_i |a_i - b_i|^2 in binary64;
+// partials: one per block.
+int launch_max_sq_diff(int da, const void* a, int db, const void* b, uint64_t n, double* partials, int nblocks,
+                       double* out, void* stream);
 // out (device, 2^k doubles): probability of each value of the listed qubits;
 // partials: 2^k per block.
 int launch_probabilities(int dtype, const void* s, uint64_t n, const QubitList& ql, double* partials, int nblocks,

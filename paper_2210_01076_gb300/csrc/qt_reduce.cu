@@ -89,6 +89,65 @@ __global__ void __launch_bounds__(kRedThreads) k_fid_partial(const void* __restr
     }
 }
 
+// |a_i - b_i|^2 in binary64: every dtype converts exactly enough (binary32
+// exactly, float-float as hi + lo rounded once, binary64 as is) that the
+// difference of two states within 1e-12 of each other is resolved.
+template <int DT>
+__device__ __forceinline__ void load_f64(const void* s, uint64_t i, double& re, double& im) {
+    if constexpr (DT == QT_C64) {
+        const float2 a = static_cast<const float2*>(s)[i];
+        re = double(a.x);
+        im = double(a.y);
+    } else if constexpr (DT == QT_C128_DF) {
+        const float4 a = static_cast<const float4*>(s)[i];
+        re = double(a.x) + double(a.y);
+        im = double(a.z) + double(a.w);
+    } else {
+        const double2 a = static_cast<const double2*>(s)[i];
+        re = a.x;
+        im = a.y;
+    }
+}
+
+__device__ __forceinline__ double block_max_d(double v, double* red) {
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_down_sync(0xffffffffu, v, o));
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    double s = 0.0;
+    if (threadIdx.x == 0)
+        for (int w = 0; w < kRedThreads / 32; ++w) s = fmax(s, red[w]);
+    return s;
+}
+
+// per block: max over its amplitudes of |a_i - b_i|^2
+template <int DA, int DB>
+__global__ void __launch_bounds__(kRedThreads) k_maxdiff_partial(const void* __restrict__ a,
+                                                                 const void* __restrict__ b, uint64_t n,
+                                                                 double* __restrict__ partials) {
+    __shared__ double red[kRedThreads / 32];
+    double m = 0.0;
+    const uint64_t stride = uint64_t(gridDim.x) * blockDim.x;
+    for (uint64_t i = blockIdx.x * uint64_t(blockDim.x) + threadIdx.x; i < n; i += stride) {
+        double ar, ai, br, bi;
+        load_f64<DA>(a, i, ar, ai);
+        load_f64<DB>(b, i, br, bi);
+        const double dr = ar - br, di = ai - bi;
+        m = fmax(m, dr * dr + di * di);
+    }
+    const double s = block_max_d(m, red);
+    if (threadIdx.x == 0) partials[blockIdx.x] = s;
+}
+
+__global__ void __launch_bounds__(kRedThreads) k_max_final(const double* __restrict__ partials, int nrows,
+                                                          double* __restrict__ out) {
+    __shared__ double red[kRedThreads / 32];
+    double m = 0.0;
+    for (int r = threadIdx.x; r < nrows; r += blockDim.x) m = fmax(m, partials[r]);
+    const double s = block_max_d(m, red);
+    if (threadIdx.x == 0) *out = s;
+}
+
 __global__ void k_sum_columns(const double* __restrict__ partials, int nrows, int ncols, double* __restrict__ out) {
     for (int col = blockIdx.x * blockDim.x + threadIdx.x; col < ncols; col += gridDim.x * blockDim.x) {
         double s = 0.0;
@@ -126,7 +185,30 @@ int launch_fid_a(int db, const void* a, const void* b, uint64_t n, double* parti
     return launch_k(k, dim3(nblocks), dim3(kRedThreads), 0, st, a, b, n, partials);
 }
 
+template <int DA>
+int launch_maxdiff_a(int db, const void* a, const void* b, uint64_t n, double* partials, int nblocks,
+                     cudaStream_t st) {
+    void (*k)(const void*, const void*, uint64_t, double*) = db == QT_C128  ? k_maxdiff_partial<DA, QT_C128>
+                                                            : db == QT_C64 ? k_maxdiff_partial<DA, QT_C64>
+                                                                           : k_maxdiff_partial<DA, QT_C128_DF>;
+    return launch_k(k, dim3(nblocks), dim3(kRedThreads), 0, st, a, b, n, partials);
+}
+
 }  // namespace
+
+int launch_max_sq_diff(int da, const void* a, int db, const void* b, uint64_t n, double* partials, int nblocks,
+                       double* out, void* stream) {
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    int rc;
+    switch (da) {
+        case QT_C128: rc = launch_maxdiff_a<QT_C128>(db, a, b, n, partials, nblocks, st); break;
+        case QT_C64: rc = launch_maxdiff_a<QT_C64>(db, a, b, n, partials, nblocks, st); break;
+        default: rc = launch_maxdiff_a<QT_C128_DF>(db, a, b, n, partials, nblocks, st); break;
+    }
+    if (rc) return rc;
+    return launch_k(k_max_final, dim3(1), dim3(kRedThreads), 0, st, static_cast<const double*>(partials), nblocks,
+                    out);
+}
 
 int reduce_blocks(uint64_t n) {
     const uint64_t blocks = (n + kRedThreads - 1) / kRedThreads;

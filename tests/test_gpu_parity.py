@@ -137,27 +137,6 @@ def test_fidelity_and_probabilities():
         cs["c64"].probabilities([1, 1])
 
 
-def test_complex64_drift_falls_back_to_complex128():
-    from paper_2210_01076_gb300.precision import AdaptiveCircuit
-    n = 12
-    levels = W.random_circuit(n, 400, seed=31, p_multi=0.4)
-    want = oracle.simulate(n, W.flatten(levels))
-    loose = AdaptiveCircuit(n, 8, drift_tol=1e-3)
-    loose.load_levels(levels)
-    loose.update_state()
-    assert loose.dtype == "c64" and loose.drift is not None and loose.drift <= 1e-3
-    assert max_err(loose.read_amplitudes(), want) <= 1e-5
-    strict = AdaptiveCircuit(n, 8, drift_tol=1e-12)
-    strict.load_levels(levels)
-    strict.update_state()
-    assert strict.dtype == "c128df" and strict.switched_at_update == 1
-    assert max_err(strict.read_amplitudes(), want) <= 1e-12
-    strict.insert_level(0)
-    strict.insert_gate(0, W.make_gate("h", [0]))
-    strict.update_state()
-    assert max_err(strict.read_amplitudes(), oracle.simulate(n, [W.make_gate("h", [0])] + W.flatten(levels))) <= 1e-12
-
-
 def test_bounded_wait_expiry_reports_timeout():
     """Failure detection without a fault: the staging copies are withheld, the
     kernel's bounded wait expires (1 s), the update reports QT_ERR_TIMEOUT, and

@@ -21,25 +21,30 @@ def built():
     B.load()
 
 
-def run_scenario(ncirc, nreq, workers, budget, seed):
+def mixed_dtype(c):
+    return "c64" if c % 2 else "c128df"
+
+
+def run_scenario(ncirc, nreq, workers, budget, seed, qubits=(9, 14), gates=(60, 160), log2_part=lambda n: min(n, 7),
+                 dtype_of=mixed_dtype, ckpt=lambda levels: 2):
     """Requests are inserts into a fresh level, or replaces of a gate present
     from the start (each at most once), so their ids are known up front."""
     rng = np.random.default_rng(seed)
-    ns = [int(rng.integers(9, 14)) for _ in range(ncirc)]
+    ns = [int(rng.integers(*qubits)) for _ in range(ncirc)]
     circuits, mirrors, server_c, ids = [], [], [], []
     for c in range(ncirc):
-        levels = W.random_circuit(ns[c], int(rng.integers(60, 160)), seed=seed * 100 + c, p_multi=0.4)
+        levels = W.random_circuit(ns[c], int(rng.integers(*gates)), seed=seed * 100 + c, p_multi=0.4)
         mirrors.append([list(lv) for lv in levels])
-        circ = B.Circuit(ns[c], "c64" if c % 2 else "c128df", min(ns[c], 7))
-        circ.set_option("ckpt_interval", 2)
+        circ = B.Circuit(ns[c], dtype_of(c), log2_part(ns[c]))
+        circ.set_option("ckpt_interval", ckpt(levels))
         ids.append(circ.load_levels(levels))
         circ.update_state()
         server_c.append(circ)
     # the same circuits again, edited through the direct ABI one request at a time ("alone")
     alone = []
     for c in range(ncirc):
-        circ = B.Circuit(ns[c], "c64" if c % 2 else "c128df", min(ns[c], 7))
-        circ.set_option("ckpt_interval", 2)
+        circ = B.Circuit(ns[c], dtype_of(c), log2_part(ns[c]))
+        circ.set_option("ckpt_interval", ckpt(mirrors[c]))
         circ.load_levels([list(lv) for lv in mirrors[c]])
         circ.update_state()
         alone.append((circ, [list(x) for x in ids[c]]))
@@ -102,6 +107,31 @@ def test_server_results_match_alone_and_oracle():
         want = oracle.simulate(ns[c], W.flatten(mirrors[c]))
         tol = 1e-5 if c % 2 else 1e-12
         assert np.max(np.abs(got.astype(np.complex128) - want)) <= tol, c
+
+
+def test_server_at_served_sizes_against_the_oracle():
+    """The served stream's shapes: complex64 circuits of 20-22 qubits and
+    about 1000 random gates with checkpoints every ~1/8 of the levels and
+    partitions of 2^16, a mix of edit requests on four workers.  Every
+    circuit ends bit-identical to the same requests made alone and within the
+    complex64 contract of the FP64 oracle over the whole state."""
+    ns, server_c, alone, mirrors, results, info = run_scenario(
+        ncirc=4, nreq=24, workers=4, budget=0, seed=21, qubits=(20, 23), gates=(900, 1101),
+        log2_part=lambda n: 16, dtype_of=lambda c: "c64", ckpt=lambda levels: max(4, -(-len(levels) // 8)))
+    assert all(r["status"] == B.QT_OK for r in results)
+    assert max(ns) >= 21
+    for c, circ in enumerate(server_c):
+        got = circ.read_amplitudes()
+        assert np.array_equal(got.view(np.uint8), alone[c][0].read_amplitudes().view(np.uint8)), c
+        want = oracle.simulate(ns[c], W.flatten(mirrors[c]), nthreads=oracle.max_threads())
+        a = got.astype(np.complex128)
+        assert np.max(np.abs(a - want)) <= 1e-5, c
+        fid = abs(np.vdot(want, a)) ** 2 / (np.vdot(a, a).real * np.vdot(want, want).real)
+        assert 1 - fid <= 1e-6, c
+    for circ in server_c:
+        circ.close()
+    for circ, _ in alone:
+        circ.close()
 
 
 def test_server_budget_evicts_and_stays_correct():
