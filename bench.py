@@ -295,15 +295,26 @@ def run_ours(args):
     value = amp_all / t_max_s
 
     # ---- full re-simulation latency on the current circuit (same plan)
-    fulls = []
+    fulls, full_passes = [], 0
     for _ in range(3):
-        fulls.append(c.update_state(force_full=True)["gpu_ms"])
+        fs = c.update_state(force_full=True)
+        fulls.append(fs["gpu_ms"])
+        full_passes = fs["passes_total"]
     inc_lat = [s["gpu_ms"] for s in stats]
-    # per-round incremental efficiency: the round's time over the time a full
-    # re-simulation takes for the work left dirty (1 = the update costs
-    # exactly its dirty fraction of a full run; below 1 = cheaper)
+    # per-round incremental efficiency: the round's time over what a full
+    # re-simulation of that round's circuit costs for the work left dirty
+    # (1 = the update costs exactly its dirty fraction of a full run).  The
+    # circuit changes a little every round, so a round's full cost is the
+    # measured full time scaled by its pass count.  Rounds with nothing dirty
+    # (no work) have no efficiency and are counted apart.
     full_p50 = pctl(fulls, 50)
-    eff = [s["gpu_ms"] / max((1.0 - s["clean_fraction"]) * full_p50, 1e-9) for s in stats]
+    eff, noop = [], 0
+    for s in stats:
+        dirty = (1.0 - s["clean_fraction"]) * full_p50 * s["passes_total"] / max(full_passes, 1)
+        if s["passes_run"] == 0 or dirty <= 0.0:
+            noop += 1
+            continue
+        eff.append(s["gpu_ms"] / dirty)
 
     # ---- end to end through the public API with host buffers: edits in,
     # update, the whole state read back to pinned host memory, every step.
@@ -386,9 +397,11 @@ def run_ours(args):
             "speedup_vs_full_p50": (pctl(fulls, 50) / pctl(inc_lat, 50)) if inc_lat else None,
             "incremental_efficiency": {
                 "p50": pctl(eff, 50), "p99": pctl(eff, 99), "max": max(eff) if eff else None,
-                "definition": "per round: incremental update time / ((1 - clean fraction) x full re-simulation time)",
+                "rounds_without_work": noop,
+                "definition": "per round: incremental update time / ((1 - clean fraction) x full re-simulation "
+                              "time of that round's circuit, the measured full time scaled by its pass count)",
                 "rounds": [{"ms": s["gpu_ms"], "clean": s["clean_fraction"], "passes_run": s["passes_run"],
-                            "launches": s["launches"]} for s in stats]},
+                            "passes_total": s["passes_total"], "launches": s["launches"]} for s in stats]},
             "accuracy": accuracy,
             "gpu_launches": launches,
             "roofline": roofline_pair(achieved, peak, peak_kind, alu_ops, kern_ms, "c128df", traffic_per_launch,

@@ -289,11 +289,18 @@ qt_status qt_norm_static(const void* amps_device, uint64_t count, int32_t dtype,
  *                    returns QT_ERR_TIMEOUT; a failure-detection test hook
  *   "reg_kernel"     1: register-resident pass kernel for tiles of 2^7 amplitudes or more
  *                    (default); 0: shared-memory pass kernel for every tile
+ *   "tc_blocks"      complex64 only: 1 = fold runs of a pass's ops that act on at most
+ *                    five tile qubits into one 32x32 block applied on the tensor cores
+ *                    (tcgen05 MMA, 3xTF32: fp32-class accuracy) inside the fused pass
+ *                    (tiles of 12 qubits); 0 (default) = every op in the register kernel
+ *   "tc_threshold"   tenths of a dense one-qubit op: a run becomes a block when the
+ *                    register kernel's estimated cost of its ops exceeds this
+ *                    (default 40); 0 makes every run a block
  *   "dry_run"        1: qt_update_state plans and tracks but launches nothing and
  *                    allocates nothing (host-logic testing); the device state is
  *                    marked stale and the next real update runs in full.
- * Changing ckpt_interval, fusion or tile_high (or a budget that changes the
- * interval) makes the next update full. */
+ * Changing ckpt_interval, fusion, tile_high, tc_blocks or tc_threshold (or a
+ * budget that changes the interval) makes the next update full. */
 qt_status qt_set_option(qt_circuit* c, const char* key, int64_t value);
 
 /* Run the circuit's GPU work on `cuda_stream` (a cudaStream_t; NULL = the
@@ -368,8 +375,13 @@ const char* qt_batch_last_error(const qt_batch* b);
  * hbm_budget_bytes (0 = no budget): a request whose circuit is not resident
  * and does not fit evicts idle circuits least-recently-used first
  * (qt_release_device), or waits while other requests proceed.  Requests on
- * one circuit run in submission order.  The caller keeps ownership of the
- * circuits and must not call into a circuit while the server may use it. */
+ * one circuit run in submission order.  With a budget, the server also sets
+ * every circuit's "ckpt_budget" option to its share of the budget (the
+ * budget less one spare state vector per circuit, divided in proportion to
+ * state size, at least two state vectors each), so that circuits stay
+ * resident rather than being evicted and re-simulated; each qt_server_add_
+ * circuit re-divides it.  The caller keeps ownership of the circuits and
+ * must not call into a circuit while the server may use it. */
 typedef struct qt_server qt_server;
 
 typedef enum {

@@ -97,6 +97,8 @@ struct qt_circuit {
     bool reg_kernel = true;
     bool tma = false;  // the bulk-copy staged persistent kernel measured slower than one CTA per tile
     bool test_stall = false;
+    bool tc_blocks = false;    // complex64: fused blocks on the tensor cores
+    int tc_threshold10 = 40;   // ... when their register-kernel cost exceeds this / 10 dense ops
 
     // committed plan (matches the slabs when device_valid)
     bool have_plan = false;
@@ -119,6 +121,10 @@ struct qt_circuit {
     size_t d_ops_cap = 0;
     uint32_t* d_wl = nullptr;
     size_t d_wl_cap = 0;
+    float* d_blk = nullptr;  // operands B of the tensor-core blocks
+    size_t d_blk_cap = 0;
+    float* h_blk = nullptr;  // pinned staging
+    size_t h_blk_cap = 0;
     DevOp* h_ops = nullptr;  // pinned staging
     size_t h_ops_cap = 0;
     uint32_t* h_wl = nullptr;
@@ -201,6 +207,12 @@ void free_device(qt_circuit* c) {
     cudaFree(c->d_wl);
     cudaFreeHost(c->h_ops);
     cudaFreeHost(c->h_wl);
+    cudaFree(c->d_blk);
+    cudaFreeHost(c->h_blk);
+    c->d_blk = nullptr;
+    c->d_blk_cap = 0;
+    c->h_blk = nullptr;
+    c->h_blk_cap = 0;
     cudaFree(c->d_norm_partials);
     cudaFree(c->d_norm_out);
     cudaFree(c->d_red);
@@ -337,15 +349,17 @@ PlanParams make_params(const qt_circuit* c) {
     pp.nh_max = std::max(0, std::min(c->tile_high, c->n - pp.lt));
     pp.fusion = c->fusion;
     pp.merge = c->merge;
+    pp.tc_blocks = c->tc_blocks && c->dtype == QT_C64 && c->reg_kernel;
+    pp.tc_threshold = c->tc_threshold10 / 10.0;
     return pp;
 }
 
 bool same_params(const PlanParams& a, const PlanParams& b) {
     return a.n == b.n && a.p == b.p && a.lt == b.lt && a.nh_max == b.nh_max && a.fusion == b.fusion &&
-           a.merge == b.merge;
+           a.merge == b.merge && a.tc_blocks == b.tc_blocks && a.tc_threshold == b.tc_threshold;
 }
 
-DevOp encode_op(int dtype, const Pass& ps, const HostOp& op) {
+DevOp encode_op(int dtype, const Pass& ps, const HostOp& op, std::vector<float>* blkbuf = nullptr) {
     DevOp d;
     std::memset(&d, 0, sizeof d);
     auto loc = [&](int q) -> int {
@@ -354,6 +368,29 @@ DevOp encode_op(int dtype, const Pass& ps, const HostOp& op) {
             if (ps.h[k] == q) return ps.lt + k;
         return -1;
     };
+    if (op.kind == OP_BLOCK) {
+        // tensor-core block: its tile bits, the other tile bits (rows), and
+        // its operand B appended to the update's block buffer
+        if (!blkbuf) throw std::logic_error("block op without a block buffer");
+        const Block& b = ps.blocks.at(size_t(op.q0));
+        d.kind = OP_BLOCK;
+        d.b0 = d.b1 = d.gq = -1;
+        BlockStage& bs = *reinterpret_cast<BlockStage*>(&d.m);
+        uint32_t in = 0;
+        for (int i = 0; i < 5; ++i) {
+            bs.s[i] = int8_t(loc(b.q[i]));
+            in |= 1u << bs.s[i];
+        }
+        int r = 0;
+        for (int t = 0; t < ps.lt + ps.nh; ++t)
+            if (!((in >> t) & 1u)) bs.rows[r++] = int8_t(t);
+        if (r != 7) throw std::logic_error("block op needs a tile of 12 bits");
+        bs.boff = int64_t(blkbuf->size() * sizeof(float));
+        const size_t at = blkbuf->size();
+        blkbuf->resize(at + kBlockBytes / sizeof(float));
+        block_operand(b, blkbuf->data() + at);
+        return d;
+    }
     uint64_t tile_mask = (uint64_t(1) << ps.lt) - 1;
     for (int k = 0; k < ps.nh; ++k) tile_mask |= uint64_t(1) << ps.h[k];
     d.kind = op.kind;
@@ -468,6 +505,7 @@ qt_status do_update(qt_circuit* c, int force_full, qt_update_stats* stats) {
     std::vector<Launch> launches;
     std::vector<DevOp> hops;
     std::vector<uint32_t> hwl;
+    std::vector<float> hblk;  // operands B of the tensor-core blocks
     std::vector<Bitset> lastF(S), lastW(S);
     uint64_t seg_amp_updates = 0;
     Bitset dirty_in;
@@ -582,7 +620,7 @@ qt_status do_update(qt_circuit* c, int force_full, qt_update_stats* stats) {
             dp.op_offset = int64_t(hops.size());
             std::vector<DevOp> pops;
             pops.reserve(ps.ops.size());
-            for (const HostOp& o : ps.ops) pops.push_back(encode_op(c->dtype, ps, o));
+            for (const HostOp& o : ps.ops) pops.push_back(encode_op(c->dtype, ps, o, &hblk));
             if (c->reg_kernel) plan_register_layout(&dp, &pops, int(bytes_per_amp(c->dtype)));
             dp.tma = (dp.reg_kernel && c->tma) ? 1 : 0;
             dp.test_stall = c->test_stall ? 1 : 0;
@@ -620,7 +658,12 @@ qt_status do_update(qt_circuit* c, int force_full, qt_update_stats* stats) {
         if ((rs = grow_device(c, &c->d_wl, &c->d_wl_cap, std::max<size_t>(hwl.size(), 1))) != QT_OK) return rs;
         if ((rs = grow_host(c, &c->h_ops, &c->h_ops_cap, std::max<size_t>(hops.size(), 1))) != QT_OK) return rs;
         if ((rs = grow_host(c, &c->h_wl, &c->h_wl_cap, std::max<size_t>(hwl.size(), 1))) != QT_OK) return rs;
-        st.h2d_bytes = hops.size() * sizeof(DevOp) + hwl.size() * sizeof(uint32_t);
+        if (!hblk.empty()) {
+            if ((rs = grow_device(c, &c->d_blk, &c->d_blk_cap, hblk.size())) != QT_OK) return rs;
+            if ((rs = grow_host(c, &c->h_blk, &c->h_blk_cap, hblk.size())) != QT_OK) return rs;
+            std::memcpy(c->h_blk, hblk.data(), hblk.size() * sizeof(float));
+        }
+        st.h2d_bytes = hops.size() * sizeof(DevOp) + hwl.size() * sizeof(uint32_t) + hblk.size() * sizeof(float);
         if (!hops.empty()) std::memcpy(c->h_ops, hops.data(), hops.size() * sizeof(DevOp));
         if (!hwl.empty()) std::memcpy(c->h_wl, hwl.data(), hwl.size() * sizeof(uint32_t));
         cudaError_t e;
@@ -636,6 +679,10 @@ qt_status do_update(qt_circuit* c, int force_full, qt_update_stats* stats) {
             (e = cudaMemcpyAsync(c->d_wl, c->h_wl, hwl.size() * sizeof(uint32_t), cudaMemcpyHostToDevice,
                                  c->stream)) != cudaSuccess)
             return cuda_fail(c, e, "upload worklists");
+        if (!hblk.empty() &&
+            (e = cudaMemcpyAsync(c->d_blk, c->h_blk, hblk.size() * sizeof(float), cudaMemcpyHostToDevice,
+                                 c->stream)) != cudaSuccess)
+            return cuda_fail(c, e, "upload blocks");
         size_t evi = 0;
         for (const Launch& ln : launches) {
             void* src = c->slabs[ln.seg];
@@ -651,7 +698,9 @@ qt_status do_update(qt_circuit* c, int force_full, qt_update_stats* stats) {
                     if (!e0 || !e1) return fail(c, QT_ERR_CUDA, "event pool");
                     cudaEventRecord(e0, c->stream);
                 }
-                rc = launch_pass(c->dtype, dst, ln.out_of_place ? src : dst, ln.dp, c->d_ops,
+                DevPass dp = ln.dp;
+                if (dp.mma) dp.blk = reinterpret_cast<const unsigned char*>(c->d_blk);
+                rc = launch_pass(c->dtype, dst, ln.out_of_place ? src : dst, dp, c->d_ops,
                                  ln.null_worklist ? nullptr : c->d_wl + ln.wl_offset, ln.ngroups, c->d_err,
                                  c->stream);
                 if (c->kernel_timing) cudaEventRecord(e1, c->stream);
@@ -727,10 +776,14 @@ qt_status check_readable(qt_circuit* c) {
 
 // ------------------------------------------------ hooks for batched runs --
 DevOp qt::encode_device_op(int dtype, const Pass& ps, const HostOp& op) { return encode_op(dtype, ps, op); }
+DevOp qt::encode_device_op(int dtype, const Pass& ps, const HostOp& op, std::vector<float>* blkbuf) {
+    return encode_op(dtype, ps, op, blkbuf);
+}
 
 void qt::circuit_plan_whole(const qt_circuit* c, std::vector<Pass>* passes, int* dtype, int* n) {
     PlanParams pp = make_params(c);
     pp.p = c->n;  // one partition: tiles may use every qubit, no coupling
+    pp.tc_blocks = false;  // the batch kernel has no tensor-core blocks
     pp.lt = std::min(c->n, tile_low_default(c->dtype));
     pp.nh_max = std::max(0, std::min(c->tile_high, c->n - pp.lt));
     std::vector<const qt_gate*> gl;
@@ -1155,6 +1208,11 @@ qt_status qt_set_option(qt_circuit* c, const char* key, int64_t value) {
         c->test_stall = value != 0;
     } else if (k == "reg_kernel") {
         c->reg_kernel = value != 0;
+    } else if (k == "tc_blocks") {
+        c->tc_blocks = value != 0;
+    } else if (k == "tc_threshold") {
+        if (value < 0 || value > 1000) return fail(c, QT_ERR_ARG, "tc_threshold must be in [0, 1000]");
+        c->tc_threshold10 = int(value);
     } else if (k == "dry_run") {
         c->dry_run = value != 0;
     } else {
@@ -1223,6 +1281,8 @@ qt_status qt_device_bytes(const qt_circuit* c, int64_t* out) {
 size_t qt::circuit_device_bytes(const qt_circuit* c) {
     return c->device_ready ? c->slabs.size() * c->state_bytes() : 0;
 }
+
+size_t qt::circuit_state_bytes(const qt_circuit* c) { return c->state_bytes(); }
 
 size_t qt::circuit_device_need(const qt_circuit* c) {
     const size_t L = c->levels.size();

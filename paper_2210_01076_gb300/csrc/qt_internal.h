@@ -28,6 +28,7 @@ enum OpKind : int32_t {
     OP_SWAP = 6,   // exchange amplitudes with (q0, q1) bits (1,0) and (0,1)
     // (7 is OP_PERM, a register-kernel layout change)
     OP_IREAL = 8,  // [[a, ib], [ic, d]] with a, b, c, d real on target q0 (RX and its products)
+    OP_BLOCK = 9,  // a 32x32 unitary on five tile qubits (Pass::blocks[q0]), applied on the tensor cores
 };
 
 // Phase sub-kinds, chosen on the host so that exact factors cost no rounding.
@@ -54,6 +55,14 @@ struct Level {
 };
 
 // ---------------------------------------------------------------- plans --
+// A fused block: the product of a run of ops acting only on five tile qubits
+// q[0..4] (block-index bit i = qubit q[i]), as a 32x32 complex matrix u
+// (row-major, re/im interleaved: 2048 doubles), built in FP64 on the host.
+struct Block {
+    int32_t q[5];
+    std::vector<double> u;
+};
+
 struct Pass {
     std::vector<HostOp> ops;
     int32_t lt = 0;                 // tile low bits: amplitudes [0, 2^lt) are contiguous
@@ -63,6 +72,7 @@ struct Pass {
     std::vector<uint32_t> supp_masks;  // partition q is touched iff (q & m) == m for some m
     bool supp_all = false;
     int32_t ngates = 0;
+    std::vector<Block> blocks;      // OP_BLOCK ops (complex64 tensor-core path)
     bool same_as(const Pass& o) const;
 };
 
@@ -77,7 +87,20 @@ struct PlanParams {
     int nh_max = 0;    // tile qubits allowed at or above lt
     bool fusion = true;
     bool merge = true;  // multiply consecutive one-qubit ops on a qubit into one 2x2
+    // complex64 only: fold runs of ops on at most five tile qubits into
+    // tensor-core blocks when their estimated register-kernel cost exceeds
+    // tc_threshold (in units of one dense one-qubit op)
+    bool tc_blocks = false;
+    double tc_threshold = 4.0;
 };
+
+// Fold runs of a pass's ops into tensor-core blocks (complex64; tiles of 12
+// qubits: lt = 7 low and 5 high).  Ops that commute with the block being
+// built (no common qubit) may be moved ahead of it.
+void fuse_blocks(Pass* ps, const PlanParams& pp);
+// Operand B of a block (64 x 64 real embedding of u, tf32 hi and lo in the
+// MMA's 128-byte-swizzled K-major shared-memory layout): kBlockBytes bytes.
+void block_operand(const Block& b, float* out);
 
 // Lower one public gate to primitive ops (A2: gate matrices and classification).
 bool lower_gate(const qt_gate& g, int n, std::vector<HostOp>* out, std::string* err);
@@ -168,7 +191,8 @@ enum RegCode : uint8_t {
     RC_DIAG_R,   // register bit a
     RC_PH_NEG, RC_PH_POS_I, RC_PH_NEG_I, RC_PH_GEN,
     RC_PH_GROUP,  // consecutive phases merged: DevOp::b1 terms (PhTerm) in the slots that follow
-    RC_NOP
+    RC_NOP,
+    RC_MMA        // fused block on the tensor cores (BlockStage in DevOp::m)
 };
 
 // Everything the register kernel reads per op besides cm_glob and the
@@ -234,6 +258,26 @@ constexpr int kTermsPerSlot = int(sizeof(DevOp) / sizeof(PhTerm));
 // group's header and its term slots never straddle two chunks.
 constexpr int kOpChunk = 64;
 
+// The tensor-core block op (RC_MMA) as the register kernel reads it, in
+// DevOp::m.  The 4096-amplitude tile is the MMA operand A: row m (128) = the
+// seven tile bits outside the block, column 2b + {re, im} (64) = block index
+// b.  A thread's amplitude at physical slot (lane, register, warp) has row
+// and block index given by XOR-ing the contributions of its set physical
+// bits and of the pending flip (all linear over GF(2)).  After the op the
+// layout is fixed: lane bit i = row bit i, warp bits 0-1 = row bits 5-6,
+// register bit k = block bit k, warp bit 2 = block bit 4.
+struct BlockStage {
+    int64_t boff;                  // byte offset of the block's operand B (tf32 hi, then lo; 32 KB)
+    uint8_t m_lane[5], k_lane[5];  // row / block-index bits contributed by each lane-id bit
+    uint8_t m_reg[5], k_reg[5];    // ... by each register-index bit
+    uint8_t m_warp[3], k_warp[3];  // ... by each warp-id bit
+    uint8_t m_flip, k_flip;        // ... by the pending flip
+    int8_t s[5];                   // tile bit of block bit i
+    int8_t rows[7];                // tile bit of row bit i
+};
+static_assert(sizeof(BlockStage) <= 64, "BlockStage fits DevOp::m");
+constexpr int kBlockBytes = 32768;  // operand B of one block: 64 x 64 tf32, hi and lo
+
 struct DevPass {
     int32_t p;             // log2 partition size
     int32_t lt;            // tile low bits
@@ -253,6 +297,9 @@ struct DevPass {
     int32_t test_stall;    // 1: withhold the staging copies so the bounded wait expires (test hook)
     int32_t groups;        // 1: the ops hold merged phase groups (RC_PH_GROUP)
     TileLayout fin;        // register kernel: the layout the tile is stored from
+    int32_t mma;           // 1: the ops hold tensor-core blocks (RC_MMA)
+    int32_t pad_mma;
+    const unsigned char* blk;  // device buffer of the blocks' B operands (mma passes)
 };
 
 // Register-kernel layout planning for one pass (host): fills the initial
@@ -295,6 +342,7 @@ void set_thread_error(const std::string& msg);
 // Serving-loop hooks (qt_api.cpp): device bytes a circuit holds, bytes its
 // next update needs, and releasing its device memory (next update is full).
 size_t circuit_device_bytes(const qt_circuit* c);
+size_t circuit_state_bytes(const qt_circuit* c);
 size_t circuit_device_need(const qt_circuit* c);
 void circuit_release_device(qt_circuit* c);
 
@@ -302,6 +350,9 @@ void circuit_release_device(qt_circuit* c);
 // one partition, and the device encoding of an op.
 void circuit_plan_whole(const qt_circuit* c, std::vector<Pass>* passes, int* dtype, int* n);
 DevOp encode_device_op(int dtype, const Pass& ps, const HostOp& op);
+// The same, for passes with tensor-core blocks: a block's operand B is
+// appended to *blkbuf and the op records its byte offset.
+DevOp encode_device_op(int dtype, const Pass& ps, const HostOp& op, std::vector<float>* blkbuf);
 
 // One pass of one circuit in a batched launch.  Work items (tiles) of all
 // passes are numbered in wavefront order: every tile of a circuit's pass i

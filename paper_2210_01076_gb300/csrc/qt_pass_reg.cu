@@ -27,6 +27,7 @@
 #include "qt_arith.cuh"
 #include "qt_internal.h"
 #include "qt_launch.cuh"
+#include "qt_tc.cuh"
 
 // This file is compiled twice: as itself, with the kernels that have no
 // merged phase groups (RC_PH_GROUP) and the library's entry points, and from
@@ -357,13 +358,183 @@ __device__ __forceinline__ TileMap<RB> layout_map(const TileLayout& L, int nwarp
     return tile_map<RB>(L.lane, L.reg, L.warp, nwarp, L.flip, lane, wid);
 }
 
+// ------------------------------------------- mbarriers and bulk copies --
+// (the TMA-staged variant below and the tensor-core block op)
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_fence_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+__device__ __forceinline__ uint64_t global_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = global_ns();
+    while (!mbar_try_wait(bar, parity))
+        if (global_ns() - t0 > 1000000000ull) return false;
+    return true;
+}
+
+__device__ __forceinline__ void bulk_g2s(void* dst_smem, const void* src_gmem, uint32_t bytes, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_addr(dst_smem)),
+        "l"(src_gmem), "r"(bytes), "r"(smem_addr(bar))
+        : "memory");
+}
+
 // Apply the pass's ops to the thread's registers x.  The host resolved
 // every op against the layout it runs in; the kernel needs a layout only at
 // OP_PERM, which carries the old one.  `tile` is the shared-memory buffer
 // for layout changes.  Every thread of the CTA must call this.
-template <class A, int RB, bool PG>
+// State of the tensor-core block op (complex64 kernel with MMA support):
+// shared-memory operands (A: the tile split into tf32 hi and lo, 2 x 32 KB;
+// B: the block's operand, 32 KB, both 1024-byte aligned), the two mbarriers
+// (operand B landed; the MMAs completed) with this thread's phase bits, the
+// accumulator's tensor-memory address and the error flag.
+struct MmaCtx {
+    unsigned char* a_sm;
+    unsigned char* b_sm;
+    uint64_t* bar_b;
+    uint64_t* bar_m;
+    uint32_t* s_ok;
+    const unsigned char* blk;
+    int* err;
+    uint32_t tmem;
+    uint32_t ph_b, ph_m;
+    bool pending;  // MMAs issued whose completion has not been seen
+    bool abort;
+};
+
+// The tensor-core block op: the tile (in registers, any layout) is written
+// to shared memory as operand A -- row = the seven tile bits outside the
+// block, columns = the block's 32 amplitudes (re, im), each value split into
+// tf32 hi and lo -- while one thread brings the block's operand B in with
+// bulk copies; one thread then issues the 3 x 8 MMAs (Ah Bh + Ah Bl + Al Bh
+// over K = 64 in steps of 8) and commits them to an mbarrier; every thread
+// waits and reads its row's 32 accumulator columns back from tensor memory:
+// warps 0-3 (TMEM lanes 32 w ..) columns 0-31 (block bit 4 = 0), warps 4-7
+// columns 32-63.  That fixes the layout after the op (BlockStage).  Every
+// wait is bounded; on expiry the op raises the error flag and the kernel
+// stops applying ops.  Returns false when aborted.
+template <class A, int RB>
+__device__ __forceinline__ bool mma_block(typename A::cx (&x)[1 << RB], const DevOp* op, uint32_t lane, uint32_t wid,
+                                          MmaCtx* mc) {
+    static_assert(RB == 4 && sizeof(typename A::amp_t) == 8, "tensor-core blocks: complex64 tiles of 4096");
+    constexpr int R = 1 << RB;
+    const BlockStage& bs = *reinterpret_cast<const BlockStage*>(&op->m);
+    __syncthreads();  // every thread is done with the A region (layout change) and the accumulator
+    if (threadIdx.x == 0) {
+        mbar_arrive_expect_tx(mc->bar_b, uint32_t(kBlockBytes));
+        const unsigned char* src = mc->blk + bs.boff;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) bulk_g2s(mc->b_sm + q * 8192, src + q * 8192, 8192u, mc->bar_b);
+    }
+    uint32_t mt = bs.m_flip, kt = bs.k_flip;
+#pragma unroll
+    for (int i = 0; i < 5; ++i)
+        if ((lane >> i) & 1u) {
+            mt ^= bs.m_lane[i];
+            kt ^= bs.k_lane[i];
+        }
+#pragma unroll
+    for (int w = 0; w < 3; ++w)
+        if ((wid >> w) & 1u) {
+            mt ^= bs.m_warp[w];
+            kt ^= bs.k_warp[w];
+        }
+    unsigned char* a_hi = mc->a_sm;
+    unsigned char* a_lo = mc->a_sm + 32768;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        uint32_t m = mt, kb = kt;
+#pragma unroll
+        for (int k = 0; k < RB; ++k)
+            if ((r >> k) & 1) {
+                m ^= bs.m_reg[k];
+                kb ^= bs.k_reg[k];
+            }
+        const uint32_t off = tc::sw128_offset(m, 2u * kb, 128u);
+        const float rh = tc::to_tf32(x[r].re), ih = tc::to_tf32(x[r].im);
+        *reinterpret_cast<float2*>(a_hi + off) = make_float2(rh, ih);
+        *reinterpret_cast<float2*>(a_lo + off) =
+            make_float2(tc::to_tf32(__fsub_rn(x[r].re, rh)), tc::to_tf32(__fsub_rn(x[r].im, ih)));
+    }
+    tc::fence_async_smem();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const bool landed = mbar_wait_bounded(mc->bar_b, mc->ph_b);
+        if (landed) {
+            tc::fence_after_sync();
+            constexpr uint32_t idesc = tc::idesc_tf32(128, 64);
+            const uint32_t ah = tc::saddr(a_hi), al = tc::saddr(a_lo);
+            const uint32_t bh = tc::saddr(mc->b_sm), bl = bh + 16384u;
+#pragma unroll
+            for (int s = 0; s < 8; ++s) {
+                const uint32_t ka = uint32_t(s >> 2) * 16384u + uint32_t(s & 3) * 32u;
+                const uint32_t kb = uint32_t(s >> 2) * 8192u + uint32_t(s & 3) * 32u;
+                tc::mma_tf32(mc->tmem, tc::sdesc_sw128(ah + ka), tc::sdesc_sw128(bh + kb), idesc, s > 0 ? 1u : 0u);
+                tc::mma_tf32(mc->tmem, tc::sdesc_sw128(ah + ka), tc::sdesc_sw128(bl + kb), idesc, 1u);
+                tc::mma_tf32(mc->tmem, tc::sdesc_sw128(al + ka), tc::sdesc_sw128(bh + kb), idesc, 1u);
+            }
+            tc::mma_commit(mc->bar_m);
+        }
+        *mc->s_ok = landed ? 1u : 0u;
+    }
+    mc->ph_b ^= 1u;
+    __syncthreads();
+    const bool issued = *mc->s_ok != 0;
+    const bool done = issued && mbar_wait_bounded(mc->bar_m, mc->ph_m);
+    if (issued) mc->ph_m ^= 1u;
+    mc->pending = issued && !done;
+    if (__syncthreads_or(!done)) {
+        if (threadIdx.x == 0) atomicExch(mc->err, 1);
+        mc->abort = true;
+        return false;
+    }
+    tc::fence_after_sync();
+    uint32_t v[32];
+    tc::tmem_ld32(mc->tmem + ((32u * (wid & 3u)) << 16) + (wid >> 2) * 32u, v);
+    tc::tmem_ld_wait();
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        x[r].re = __uint_as_float(v[2 * r]);
+        x[r].im = __uint_as_float(v[2 * r + 1]);
+    }
+    tc::fence_before_sync();
+    return true;
+}
+
+template <class A, int RB, bool PG, bool MG = false>
 __device__ __forceinline__ void run_ops(typename A::cx (&x)[1 << RB], const DevOp* __restrict__ pops, int nops,
-                                        uint64_t base, uint32_t lane, uint32_t wid, typename A::amp_t* tile) {
+                                        uint64_t base, uint32_t lane, uint32_t wid, typename A::amp_t* tile,
+                                        MmaCtx* mc = nullptr) {
     using RO = RegOps<A, RB>;
     using cx = typename A::cx;
     constexpr int R = 1 << RB;
@@ -399,6 +570,12 @@ __device__ __forceinline__ void run_ops(typename A::cx (&x)[1 << RB], const DevO
 #pragma unroll
             for (int r = 0; r < R; ++r) x[r] = A::ld(tile[to.idx(r)]);
             continue;
+        }
+        if constexpr (MG) {
+            if (h.code == RC_MMA) {
+                if (!mma_block<A, RB>(x, op, lane, wid, mc)) return;
+                continue;
+            }
         }
         if (h.ren > 0) {
             // target on register bit ren: bring it to register bit 0 (the
@@ -487,11 +664,16 @@ constexpr int reg_min_blocks() {
             (1 << RB) * int(sizeof(typename A::amp_t)) / 4 <= 32) ? 4 : 1;
 }
 
-template <class A, int RB, bool PG>
-__global__ void __launch_bounds__(256, reg_min_blocks<A, RB>()) k_pass_reg(typename A::amp_t* dst,
+// Dynamic shared memory of the kernel with tensor-core blocks: operand A
+// (64 KB, also the layout-change buffer), operand B (32 KB), and slack to
+// align both to 1024 bytes (the 128-byte swizzle's repeat).
+constexpr size_t kMmaSmemBytes = 1024 + 65536 + size_t(kBlockBytes);
+
+template <class A, int RB, bool PG, bool MG = false>
+__global__ void __launch_bounds__(256, MG ? 2 : reg_min_blocks<A, RB>()) k_pass_reg(typename A::amp_t* dst,
                                                    const typename A::amp_t* src, const DevPass dp,
                                                    const DevOp* __restrict__ ops,
-                                                   const uint32_t* __restrict__ worklist) {
+                                                   const uint32_t* __restrict__ worklist, int* err) {
     using amp_t = typename A::amp_t;
     using cx = typename A::cx;
     constexpr int R = 1 << RB;
@@ -499,6 +681,36 @@ __global__ void __launch_bounds__(256, reg_min_blocks<A, RB>()) k_pass_reg(typen
     amp_t* tile = reinterpret_cast<amp_t*>(smem_raw);
     __shared__ uint64_t choff[1 << kMaxTileHigh];
     const uint32_t lane = threadIdx.x & 31u, wid = threadIdx.x >> 5;
+    MmaCtx mc;
+    if constexpr (MG) {
+        // operands at 1024-byte boundaries; the accumulator in tensor memory
+        __shared__ __align__(8) uint64_t bars[2];
+        __shared__ uint32_t s_tmem, s_ok;
+        const uint32_t pad = (1024u - (tc::saddr(smem_raw) & 1023u)) & 1023u;
+        mc.a_sm = smem_raw + pad;
+        mc.b_sm = mc.a_sm + 65536;
+        mc.bar_b = &bars[0];
+        mc.bar_m = &bars[1];
+        mc.s_ok = &s_ok;
+        mc.blk = dp.blk;
+        mc.err = err;
+        mc.ph_b = mc.ph_m = 0;
+        mc.pending = mc.abort = false;
+        tile = reinterpret_cast<amp_t*>(mc.a_sm);
+        if (threadIdx.x == 0) {
+            mbar_init(mc.bar_b, 1);
+            mbar_init(mc.bar_m, 1);
+            mbar_fence_init();
+        }
+        if (wid == 0) {
+            tc::tmem_alloc(&s_tmem, tc::kTmemCols);
+            tc::tmem_relinquish();
+        }
+        tc::fence_before_sync();
+        __syncthreads();
+        tc::fence_after_sync();
+        mc.tmem = s_tmem;
+    }
     const uint64_t base = tile_base(dp, worklist, blockIdx.x);
     chunk_offsets(dp, choff);
     __syncthreads();
@@ -512,16 +724,29 @@ __global__ void __launch_bounds__(256, reg_min_blocks<A, RB>()) k_pass_reg(typen
             x[r] = A::ld(src[base | choff[j >> dp.lt] | (j & lowmask)]);
         }
     }
-    run_ops<A, RB, PG>(x, ops + dp.op_offset, dp.nops, base, lane, wid, tile);
+    run_ops<A, RB, PG, MG>(x, ops + dp.op_offset, dp.nops, base, lane, wid, tile, &mc);
     // A pass whose gates were all relabels has no ops, so no barrier has
     // separated the loads from the stores; its final layout sends amplitudes
     // to positions that other warps of the CTA load (in place: dst == src).
     if (dp.nops == 0) __syncthreads();
-    const TileMap<RB> m = layout_map<RB>(dp.fin, dp.nwarp, lane, wid);
+    if (!MG || !mc.abort) {
+        const TileMap<RB> m = layout_map<RB>(dp.fin, dp.nwarp, lane, wid);
 #pragma unroll
-    for (int r = 0; r < R; ++r) {
-        const uint32_t j = m.idx(r);
-        dst[base | choff[j >> dp.lt] | (j & lowmask)] = A::st(x[r]);
+        for (int r = 0; r < R; ++r) {
+            const uint32_t j = m.idx(r);
+            dst[base | choff[j >> dp.lt] | (j & lowmask)] = A::st(x[r]);
+        }
+    }
+    if constexpr (MG) {
+        // an aborted block may still have MMAs in flight: wait for them
+        // (bounded) before the accumulator's memory is given back
+        if (threadIdx.x == 0 && mc.pending) mbar_wait_bounded(mc.bar_m, mc.ph_m);
+        tc::fence_before_sync();
+        __syncthreads();
+        if (wid == 0) {
+            tc::fence_after_sync();
+            tc::tmem_dealloc(mc.tmem, tc::kTmemCols);
+        }
     }
 }
 
@@ -532,55 +757,6 @@ __global__ void __launch_bounds__(256, reg_min_blocks<A, RB>()) k_pass_reg(typen
 // second shared-memory buffer, so HBM reads overlap the arithmetic.  Every
 // wait on the mbarrier is bounded (1 s of %globaltimer); on expiry the CTA
 // raises the error flag and returns, and the host reports QT_ERR_TIMEOUT.
-__device__ __forceinline__ uint32_t smem_addr(const void* p) {
-    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-
-__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void mbar_fence_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
-
-__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
-                 : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(smem_addr(bar)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-
-__device__ __forceinline__ uint64_t global_ns() {
-    uint64_t t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
-    if (mbar_try_wait(bar, parity)) return true;
-    const uint64_t t0 = global_ns();
-    while (!mbar_try_wait(bar, parity))
-        if (global_ns() - t0 > 1000000000ull) return false;
-    return true;
-}
-
-__device__ __forceinline__ void bulk_g2s(void* dst_smem, const void* src_gmem, uint32_t bytes, uint64_t* bar) {
-    asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-            smem_addr(dst_smem)),
-        "l"(src_gmem), "r"(bytes), "r"(smem_addr(bar))
-        : "memory");
-}
-
 template <class A, int RB, bool PG>
 __global__ void __launch_bounds__(256, (RB <= 3 ? 3 : 1)) k_pass_tma(typename A::amp_t* dst,
                                                    const typename A::amp_t* src, const DevPass dp,
@@ -654,6 +830,22 @@ int launch_reg_t(void* dst, const void* src, const DevPass& dp, const DevOp* ops
     const unsigned threads = 32u << dp.nwarp;
     if (nblocks > 0x7fffffffull || tile_bytes > 64 * 1024 || dp.nreg != RB) return int(cudaErrorInvalidConfiguration);
     const bool tma = dp.tma && err != nullptr && (uint32_t(sizeof(amp_t)) << dp.lt) % 16 == 0;
+    if (dp.mma) {
+        // tensor-core blocks: complex64 tiles of 4096 amplitudes only
+        if constexpr (std::is_same<A, ArF32>::value && RB == 4) {
+            if (dp.blk == nullptr || err == nullptr || threads != 256) return int(cudaErrorInvalidConfiguration);
+            static DeviceOnce mattr;
+            const int rc = mattr.run([](int) {
+                return int(cudaFuncSetAttribute(k_pass_reg<A, RB, PG, true>,
+                                                cudaFuncAttributeMaxDynamicSharedMemorySize, int(kMmaSmemBytes)));
+            });
+            if (rc) return rc;
+            return launch_k(k_pass_reg<A, RB, PG, true>, dim3(unsigned(nblocks)), dim3(threads), kMmaSmemBytes, st,
+                            static_cast<amp_t*>(dst), static_cast<const amp_t*>(src), dp, ops, worklist, err);
+        } else {
+            return int(cudaErrorInvalidConfiguration);
+        }
+    }
     if (!tma) {
         static DeviceOnce attr;
         const int rc = attr.run([](int) {
@@ -662,7 +854,7 @@ int launch_reg_t(void* dst, const void* src, const DevPass& dp, const DevOp* ops
         });
         if (rc) return rc;
         return launch_k(k_pass_reg<A, RB, PG>, dim3(unsigned(nblocks)), dim3(threads), tile_bytes, st,
-                        static_cast<amp_t*>(dst), static_cast<const amp_t*>(src), dp, ops, worklist);
+                        static_cast<amp_t*>(dst), static_cast<const amp_t*>(src), dp, ops, worklist, err);
     }
     static DeviceOnce tattr;
     int rc = tattr.run([](int) {

@@ -233,7 +233,11 @@ bool lower_gate(const qt_gate& g, int n, std::vector<HostOp>* out, std::string* 
 }
 
 bool Pass::same_as(const Pass& o) const {
-    if (lt != o.lt || nh != o.nh || ops.size() != o.ops.size()) return false;
+    if (lt != o.lt || nh != o.nh || ops.size() != o.ops.size() || blocks.size() != o.blocks.size()) return false;
+    for (size_t b = 0; b < blocks.size(); ++b) {
+        if (std::memcmp(blocks[b].q, o.blocks[b].q, sizeof blocks[b].q) != 0 || blocks[b].u != o.blocks[b].u)
+            return false;
+    }
     for (int k = 0; k < nh; ++k)
         if (h[k] != o.h[k]) return false;
     for (size_t i = 0; i < ops.size(); ++i) {
@@ -356,9 +360,178 @@ SegPlan plan_segment(const std::vector<const qt_gate*>& gates, const PlanParams&
             ps.supp_masks.push_back(pm);
         }
         if (ps.ops.empty()) ps.supp_all = false;  // a pass reduced to nothing touches nothing
+        if (pp.tc_blocks && ps.lt == 7 && ps.nh == 5) fuse_blocks(&ps, pp);
         if (ps.ngates > 0) sp.passes.push_back(std::move(ps));
     }
     return sp;
+}
+
+// ------------------------------------------------------ tensor-core blocks --
+namespace {
+
+// Register-kernel cost of an op in units of one dense one-qubit op
+// (complex64, measured per-op costs: dense 2x2 0.13 SM-cycles per amplitude,
+// real 2x2 ~0.09, controlled phases and exchanges ~0.05, relabels ~0).
+double reg_cost(const HostOp& op) {
+    switch (op.kind) {
+        case OP_DENSE: return 1.0;
+        case OP_REAL: case OP_IREAL: case OP_ANTI: case OP_DIAG: return 0.7;
+        case OP_PHASE: return 0.4;
+        case OP_X: case OP_SWAP: return op.cmask ? 0.6 : 0.05;
+        default: return 1.0;
+    }
+}
+
+// Apply op (acting on qubits inside the block) to the columns of the 32x32
+// matrix u (row-major complex): u := M_op u.  pos[q] = block bit of qubit q.
+void block_apply(std::vector<cd>& u, const HostOp& op, const int* pos) {
+    uint32_t cm = 0;
+    for (int q = 0; q < 64; ++q)
+        if ((op.cmask >> q) & 1) cm |= 1u << pos[q];
+    auto ok = [&](uint32_t r) { return (r & cm) == cm; };
+    for (int col = 0; col < 32; ++col) {
+        auto U = [&](uint32_t r) -> cd& { return u[size_t(r) * 32 + col]; };
+        switch (op.kind) {
+            case OP_DENSE: case OP_REAL: case OP_IREAL: case OP_X: case OP_ANTI: {
+                const uint32_t t = 1u << pos[op.q0];
+                M2 m;
+                op_matrix(op, &m);
+                for (uint32_t r = 0; r < 32; ++r) {
+                    if ((r & t) || !ok(r)) continue;
+                    const cd a = U(r), b = U(r | t);
+                    U(r) = m.a[0] * a + m.a[1] * b;
+                    U(r | t) = m.a[2] * a + m.a[3] * b;
+                }
+                break;
+            }
+            case OP_SWAP: {
+                const uint32_t t0 = 1u << pos[op.q0], t1 = 1u << pos[op.q1];
+                for (uint32_t r = 0; r < 32; ++r)
+                    if ((r & t0) && !(r & t1) && ok(r)) std::swap(U(r), U(r ^ t0 ^ t1));
+                break;
+            }
+            case OP_DIAG: {
+                const uint32_t t = 1u << pos[op.q0];
+                for (uint32_t r = 0; r < 32; ++r)
+                    if (ok(r)) U(r) *= (r & t) ? get(op.m, 1) : get(op.m, 0);
+                break;
+            }
+            case OP_PHASE:
+                for (uint32_t r = 0; r < 32; ++r)
+                    if (ok(r)) U(r) *= get(op.m, 0);
+                break;
+            default: break;
+        }
+    }
+}
+
+}  // namespace
+
+void fuse_blocks(Pass* ps, const PlanParams& pp) {
+    uint64_t tile = (uint64_t(1) << ps->lt) - 1;
+    for (int k = 0; k < ps->nh; ++k) tile |= uint64_t(1) << ps->h[k];
+    std::vector<HostOp> out;
+    std::vector<HostOp> cur;
+    uint64_t cq = 0;
+    double ccost = 0.0;
+    auto flush = [&]() {
+        if (cur.empty()) return;
+        if (ccost < pp.tc_threshold) {
+            for (const HostOp& o : cur) out.push_back(o);
+        } else {
+            // pad to five qubits with the highest other tile qubits (the rows
+            // keep the low ones, which become lane bits: coalesced stores)
+            Block b;
+            int nq = 0;
+            for (int q = 0; q < 64; ++q)
+                if ((cq >> q) & 1) b.q[nq++] = q;
+            for (int q = 63; q >= 0 && nq < 5; --q)
+                if (((tile >> q) & 1) && !((cq >> q) & 1)) {
+                    cq |= uint64_t(1) << q;
+                    b.q[nq++] = q;
+                }
+            std::sort(b.q, b.q + 5);
+            int pos[64];
+            for (int i = 0; i < 5; ++i) pos[b.q[i]] = i;
+            std::vector<cd> u(32 * 32, cd(0.0, 0.0));
+            for (int i = 0; i < 32; ++i) u[size_t(i) * 32 + i] = 1.0;
+            int ng = 0;
+            for (const HostOp& o : cur) {
+                block_apply(u, o, pos);
+                ng += o.ngates;
+            }
+            b.u.resize(2 * 32 * 32);
+            for (size_t i = 0; i < u.size(); ++i) {
+                b.u[2 * i] = u[i].real();
+                b.u[2 * i + 1] = u[i].imag();
+            }
+            HostOp bo;
+            bo.kind = OP_BLOCK;
+            bo.q0 = int32_t(ps->blocks.size());
+            bo.cmask = 0;
+            bo.ngates = ng;
+            ps->blocks.push_back(std::move(b));
+            out.push_back(bo);
+        }
+        cur.clear();
+        cq = 0;
+        ccost = 0.0;
+    };
+    for (const HostOp& o : ps->ops) {
+        const uint64_t q = op_qubits(o);
+        const bool eligible = (q & ~tile) == 0 && o.kind != OP_BLOCK;
+        if (eligible && popcount64(cq | q) <= 5) {
+            cur.push_back(o);
+            cq |= q;
+            ccost += reg_cost(o);
+            continue;
+        }
+        if (!eligible && (q & cq) == 0) {  // commutes with every op of the block: runs before it
+            out.push_back(o);
+            continue;
+        }
+        flush();
+        if (eligible) {
+            cur.push_back(o);
+            cq = q;
+            ccost = reg_cost(o);
+        } else {
+            out.push_back(o);
+        }
+    }
+    flush();
+    ps->ops.swap(out);
+}
+
+void block_operand(const Block& b, float* out) {
+    auto tf32 = [](float f) {  // round to the nearest tf32 (10 fraction bits), ties away from zero
+        uint32_t u;
+        std::memcpy(&u, &f, 4);
+        u = (u + 0x1000u) & ~0x1FFFu;
+        float r;
+        std::memcpy(&r, &u, 4);
+        return r;
+    };
+    std::memset(out, 0, kBlockBytes);
+    float* hi = out;
+    float* lo = out + kBlockBytes / 8;
+    for (int n = 0; n < 64; ++n) {
+        for (int k = 0; k < 64; ++k) {
+            // real embedding: out(2j'+c') = sum_k W[n][k] in(2j+c)
+            const int jo = n >> 1, ji = k >> 1;
+            const double ur = b.u[2 * (size_t(jo) * 32 + ji)], ui = b.u[2 * (size_t(jo) * 32 + ji) + 1];
+            const int co = n & 1, ci = k & 1;
+            const double w = co == 0 ? (ci == 0 ? ur : -ui) : (ci == 0 ? ui : ur);
+            const float h = tf32(float(w));
+            const float l = tf32(float(w - double(h)));
+            // K-major, 128-byte swizzle: two K atoms of 32 elements, rows of 128 B,
+            // 16-byte chunk c of row n stored at chunk c ^ (n % 8)
+            const size_t byte = size_t(k / 32) * 8192 + size_t(n / 8) * 1024 + size_t(n % 8) * 128 +
+                                size_t((((k % 32) / 4) ^ (n % 8)) * 16) + size_t(k % 4) * 4;
+            hi[byte / 4] = h;
+            lo[byte / 4] = l;
+        }
+    }
 }
 
 // ------------------------------------------------------------ bitsets ---
@@ -603,9 +776,16 @@ void plan_register_layout(DevPass* dp, std::vector<DevOp>* ops_io, int coef_byte
         switch (o.kind) {
             case OP_DENSE: case OP_REAL: case OP_IREAL: case OP_X: case OP_ANTI: return 1u << o.b0;
             case OP_SWAP: return (1u << o.b0) | (1u << o.b1);
-            default: return 0u;
+            default: return 0u;  // a tensor-core block reads any layout
         }
     };
+    auto block_bits = [](const DevOp& o) -> uint32_t {
+        const BlockStage& bs = *reinterpret_cast<const BlockStage*>(&o.m);
+        uint32_t m = 0;
+        for (int i = 0; i < 5; ++i) m |= 1u << bs.s[i];
+        return m;
+    };
+    dp->mma = 0;
     auto pc = [](uint32_t x) { return __builtin_popcount(x); };
     std::vector<char> done(ops.size(), 0);
     // register set of a new layout for op i and the ops not yet placed after
@@ -682,6 +862,7 @@ void plan_register_layout(DevPass* dp, std::vector<DevOp>* ops_io, int coef_byte
         // factor per tile and touches none)
         qm[i] = targets(ops[i]) | ops[i].cm_tile;
         if (ops[i].kind == OP_DIAG && ops[i].b0 >= 0) qm[i] |= 1u << ops[i].b0;
+        if (ops[i].kind == OP_BLOCK) qm[i] = block_bits(ops[i]);
         dg[i] = ops[i].kind == OP_DIAG || ops[i].kind == OP_PHASE;
     }
     auto commute = [&](size_t i, size_t j) { return (qm[i] & qm[j]) == 0 || (dg[i] && dg[j]); };
@@ -711,6 +892,47 @@ void plan_register_layout(DevPass* dp, std::vector<DevOp>* ops_io, int coef_byte
         for (size_t j = i + 1; j < n; ++j)
             if (!done[j] && !commute(i, j)) --npred[j];
         DevOp o = ops[i];
+        if (o.kind == OP_BLOCK) {
+            // tensor-core block: record where each physical bit's tile bit goes
+            // (row or block index), then take the fixed post-MMA layout
+            BlockStage& bs = *reinterpret_cast<BlockStage*>(&o.m);
+            auto contrib = [&](int t, uint8_t* mrow, uint8_t* kblk) {
+                *mrow = 0;
+                *kblk = 0;
+                for (int i = 0; i < 5; ++i)
+                    if (bs.s[i] == t) *kblk = uint8_t(1u << i);
+                for (int i = 0; i < 7; ++i)
+                    if (bs.rows[i] == t) *mrow = uint8_t(1u << i);
+            };
+            for (int b = 0; b < 5; ++b) contrib(L.lane[b], &bs.m_lane[b], &bs.k_lane[b]);
+            for (int k = 0; k < nreg; ++k) contrib(L.reg[k], &bs.m_reg[k], &bs.k_reg[k]);
+            for (int w = 0; w < nwarp; ++w) contrib(L.warp[w], &bs.m_warp[w], &bs.k_warp[w]);
+            bs.m_flip = 0;
+            bs.k_flip = 0;
+            for (int t = 0; t < tb; ++t) {
+                if (!((L.flip >> t) & 1u)) continue;
+                uint8_t mr, kb;
+                contrib(t, &mr, &kb);
+                bs.m_flip ^= mr;
+                bs.k_flip ^= kb;
+            }
+            std::memset(&L, 0, sizeof L);
+            for (int b = 0; b < 5; ++b) L.lane[b] = bs.rows[b];
+            for (int k = 0; k < 4; ++k) L.reg[k] = bs.s[k];
+            L.warp[0] = bs.rows[5];
+            L.warp[1] = bs.rows[6];
+            L.warp[2] = bs.s[4];
+            for (int b = 0; b < 5; ++b) where[L.lane[b]] = b;
+            for (int k = 0; k < 4; ++k) where[L.reg[k]] = 8 + k;
+            for (int w = 0; w < 3; ++w) where[L.warp[w]] = 16 + w;
+            cur = 0;
+            for (int k = 0; k < 4; ++k) cur |= 1u << L.reg[k];
+            std::memset(&o.rh, 0, sizeof o.rh);
+            o.rh.code = RC_MMA;
+            dp->mma = 1;
+            out.push_back(o);
+            continue;
+        }
         if (relabel(o)) {
             if (o.kind == OP_X) {
                 L.flip ^= 1u << o.b0;

@@ -12,6 +12,14 @@
 // full one); a request that cannot fit yet waits without blocking others.
 // Requests on one circuit run in submission order, so a circuit's results do
 // not depend on what else is in the mix.
+//
+// With a budget, the server also sizes every circuit's checkpoints to its
+// share of the budget (the circuit's ckpt_budget option): the budget minus
+// one spare state vector per circuit is divided in proportion to the
+// circuits' state sizes, each getting room for its state and at least one
+// checkpoint.  An evicted circuit's next request re-simulates it in full,
+// which costs far more than the longer segments of fewer checkpoints, so
+// the circuits stay resident whenever their states fit together.
 #include <algorithm>
 #include <chrono>
 #include <condition_variable>
@@ -43,7 +51,9 @@ struct Slot {
     qt_circuit* c = nullptr;
     bool busy = false;
     uint64_t last_used = 0;
-    size_t bytes = 0;  // device bytes held (as of its last request)
+    size_t bytes = 0;          // device bytes held (as of its last request)
+    size_t state_bytes = 0;    // one state vector
+    int64_t ckpt_budget = 0;   // its share of the budget (0: no budget), applied before its next request
 };
 }  // namespace
 
@@ -142,9 +152,12 @@ void worker_main(qt_server* s) {
         if (!r) return;
         Slot& sl = s->slots[r->slot];
         qt_circuit* c = sl.c;
+        const int64_t ckpt_budget = sl.ckpt_budget;
         lk.unlock();
         r->t_start = Clock::now();
-        qt_status st = apply_edits(c, r->edits, &r->result);
+        qt_status st = QT_OK;
+        if (ckpt_budget > 0) st = qt_set_option(c, "ckpt_budget", ckpt_budget);
+        if (st == QT_OK) st = apply_edits(c, r->edits, &r->result);
         if (st == QT_OK) st = qt_update_state(c, 0, &r->result.stats);
         r->t_done = Clock::now();
         lk.lock();
@@ -202,10 +215,25 @@ qt_status qt_server_add_circuit(qt_server* s, qt_circuit* c, int32_t* slot) {
     Slot sl;
     sl.c = c;
     sl.bytes = circuit_device_bytes(c);
+    sl.state_bytes = circuit_state_bytes(c);
     sl.last_used = ++s->clock;
     s->resident += sl.bytes;
     s->slots.push_back(sl);
     *slot = int32_t(s->slots.size()) - 1;
+    if (s->budget > 0) {
+        // checkpoint shares: (budget - one spare state per circuit) split by
+        // state size, at least the state and one checkpoint each
+        double states = 0.0;
+        for (const Slot& o : s->slots) states += double(o.state_bytes);
+        const double pool = double(s->budget) - states;
+        for (Slot& o : s->slots) {
+            const double share = pool > 0.0 ? pool * double(o.state_bytes) / states : 0.0;
+            o.ckpt_budget = int64_t(std::max(share, 2.0 * double(o.state_bytes)));
+            // an idle circuit takes its share now (admission sizes its need
+            // from it); a busy one from its worker before its next request
+            if (!o.busy) qt_set_option(o.c, "ckpt_budget", o.ckpt_budget);
+        }
+    }
     return QT_OK;
 }
 

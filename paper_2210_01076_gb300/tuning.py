@@ -6,7 +6,9 @@ The planner's knobs trade HBM passes against per-pass work: ``tile_high``
 trades memory and incremental restart distance against nothing at all in a
 full run).  Which setting is fastest depends on the dtype (float-float
 arithmetic is issue-bound, complex64 closer to HBM-bound) and on the circuit,
-so these helpers time candidate settings on the device and keep the best.
+so these helpers time candidate settings on the device and keep the best
+-- for complex64 also whether runs of gates on five qubits go to the tensor
+cores as fused blocks (``tc_blocks``, ``tc_threshold``).
 Only the timing loop is host code; every measured run is the library's.
 """
 from __future__ import annotations
@@ -28,14 +30,19 @@ def _full_ms(c: "B.Circuit", repeats: int) -> float:
 
 def tune_circuit(n: int, dtype: str, levels, log2_partition: Optional[int] = None,
                  tile_high: Iterable[int] = (3, 4, 5), ckpt_interval: Iterable[int] = (4,),
-                 fusion: Iterable[int] = (1,), merge: Iterable[int] = (0, 1), repeats: int = 2) -> Dict:
+                 fusion: Iterable[int] = (1,), merge: Iterable[int] = (0, 1), tc_threshold: Iterable[int] = (-1,),
+                 repeats: int = 2) -> Dict:
     """Time a full simulation of ``levels`` for every combination of the
-    candidate options; return the fastest and the whole table."""
+    candidate options; return the fastest and the whole table.
+    ``tc_threshold``: -1 = no tensor-core blocks, else blocks (complex64)
+    with that threshold (tenths of a dense one-qubit op)."""
     table: List[Dict] = []
-    for th, ck, fu, me in itertools.product(tile_high, ckpt_interval, fusion, merge):
+    for th, ck, fu, me, tc in itertools.product(tile_high, ckpt_interval, fusion, merge, tc_threshold):
         c = B.Circuit(n, dtype, log2_partition)
         try:
             opts = {"tile_high": th, "ckpt_interval": ck, "fusion": fu, "merge": me}
+            if tc >= 0:
+                opts.update({"tc_blocks": 1, "tc_threshold": tc})
             for k, v in opts.items():
                 c.set_option(k, v)
             c.load_levels(levels)

@@ -11,7 +11,10 @@
 //              kernel's semantics on a physical tile, then stored through the
 //              final layout.
 // Both use exact binary64 complex arithmetic on random tile contents; the
-// results must agree to rounding.  This pins the planner's bookkeeping on the
+// results must agree to rounding.  A second part plans complex64-shaped
+// passes (tiles of 12 qubits) with tensor-core blocks and checks the fused
+// blocks (their FP64 matrices, the ops moved ahead of them, the staging
+// masks and the layout after each block) the same way.  This pins the planner's bookkeeping on the
 // CPU; the GPU parity tests pin the kernels against the oracle.
 //
 // Build: g++ -O1 -std=c++17 -I<include> -I<csrc> -I<cuda include>
@@ -105,8 +108,10 @@ static uint32_t layout_index(const int8_t* lane, const int8_t* reg, const int8_t
 }
 
 static long g_groups = 0;  // merged phase groups seen
+static long g_blocks = 0;  // tensor-core blocks seen
 
-static void run_planned(const std::vector<DevOp>& ops, const DevPass& dp, std::vector<cd>& T, uint64_t base) {
+static void run_planned(const std::vector<DevOp>& ops, const DevPass& dp, std::vector<cd>& T, uint64_t base,
+                        const std::vector<Block>* blocks = nullptr) {
     Phys P{dp.nreg, dp.nwarp, 1 << dp.nreg, 1 << dp.nwarp, {}};
     P.v.assign(size_t(32) * P.R * P.W, 0.0);
     int8_t reg0[8], warp0[8];
@@ -154,6 +159,35 @@ static void run_planned(const std::vector<DevOp>& ops, const DevPass& dp, std::v
             }
             oi += nslots;
             ++g_groups;
+            continue;
+        }
+        if (h.code == RC_MMA) {
+            // the block on the tensor cores: gather the 128 x 32 operand through
+            // the op's bit contributions, multiply by the block's matrix, and
+            // scatter through the fixed layout that follows the op
+            const BlockStage& bs = *reinterpret_cast<const BlockStage*>(&o.m);
+            const Block& blk = blocks->at(size_t(bs.boff / kBlockBytes));
+            std::vector<cd> Am(128 * 32), Dm(128 * 32, 0.0);
+            for (int w = 0; w < P.W; ++w)
+                for (int r = 0; r < P.R; ++r)
+                    for (int l = 0; l < 32; ++l) {
+                        uint32_t m = bs.m_flip, kb = bs.k_flip;
+                        for (int i = 0; i < 5; ++i)
+                            if ((l >> i) & 1) m ^= bs.m_lane[i], kb ^= bs.k_lane[i];
+                        for (int k = 0; k < P.nreg; ++k)
+                            if ((r >> k) & 1) m ^= bs.m_reg[k], kb ^= bs.k_reg[k];
+                        for (int k = 0; k < P.nwarp; ++k)
+                            if ((w >> k) & 1) m ^= bs.m_warp[k], kb ^= bs.k_warp[k];
+                        Am[m * 32 + kb] = P.at(l, r, w);
+                    }
+            for (int m = 0; m < 128; ++m)
+                for (int jo = 0; jo < 32; ++jo)
+                    for (int ji = 0; ji < 32; ++ji)
+                        Dm[m * 32 + jo] += cd(blk.u[2 * (jo * 32 + ji)], blk.u[2 * (jo * 32 + ji) + 1]) * Am[m * 32 + ji];
+            for (int w = 0; w < P.W; ++w)
+                for (int r = 0; r < P.R; ++r)
+                    for (int l = 0; l < 32; ++l) P.at(l, r, w) = Dm[(l | ((w & 3) << 5)) * 32 + (r | ((w >> 2) << 4))];
+            ++g_blocks;
             continue;
         }
         if (h.code == RC_PERM) {
@@ -357,6 +391,99 @@ int main(int argc, char** argv) {
         std::printf("no merged phase group was planned\n");
         return 1;
     }
-    std::printf("OK %ld %ld %ld\n", npasses, nops, g_groups);
+    // Tensor-core blocks (complex64 tiles of 12 qubits: 7 low, 5 high): the
+    // passes planned with and without blocks cover the same gates; the
+    // unfused ops applied directly must equal the planned ops with the
+    // blocks' FP64 matrices.
+    long nblk_passes = 0;
+    for (int ci = 0; ci < ncirc; ++ci) {
+        const int n = 12 + ci % 3;
+        std::vector<qt_gate> gates;
+        static const int pool[] = {QT_H, QT_U3, QT_U3, QT_RX, QT_RY, QT_RZ, QT_T, QT_X, QT_Y, QT_CNOT, QT_CZ, QT_CP,
+                                   QT_SWAP, QT_CCX};
+        const int ngates = 150 + 10 * (ci % 4);
+        for (int gi = 0; gi < ngates; ++gi) {
+            qt_gate g{};
+            g.kind = pool[rng() % (sizeof pool / sizeof pool[0])];
+            const int nt = g.kind == QT_SWAP ? 2 : 1;
+            const int nc = g.kind == QT_CCX ? 2 : (g.kind == QT_CNOT || g.kind == QT_CZ || g.kind == QT_CP) ? 1 : 0;
+            // qubits mostly from a window of 6, so that runs on five qubits form
+            const int lo = int(rng() % uint64_t(n - 5));
+            int q[3];
+            for (int k = 0; k < nt + nc; ++k) {
+                bool fresh;
+                do {
+                    q[k] = (rng() % 4 == 0) ? int(rng() % uint64_t(n)) : lo + int(rng() % 6);
+                    fresh = true;
+                    for (int m = 0; m < k; ++m) fresh = fresh && q[m] != q[k];
+                } while (!fresh);
+            }
+            g.ntarget = nt;
+            g.ncontrol = nc;
+            for (int k = 0; k < nt; ++k) g.target[k] = q[k];
+            for (int k = 0; k < nc; ++k) g.control[k] = q[nt + k];
+            for (int k = 0; k < 3; ++k) g.theta[k] = ang(rng);
+            gates.push_back(g);
+        }
+        std::vector<const qt_gate*> gl;
+        for (const qt_gate& g : gates) gl.push_back(&g);
+        PlanParams pp;
+        pp.n = n;
+        pp.p = n - 2;  // tiles reach into the partition index: coupled partitions
+        pp.lt = 7;
+        pp.nh_max = 5;
+        pp.fusion = true;
+        pp.merge = ci % 2 == 0;
+        SegPlan plain = plan_segment(gl, pp);
+        pp.tc_blocks = true;
+        pp.tc_threshold = ci % 3 == 0 ? 0.0 : 2.0;
+        SegPlan fused = plan_segment(gl, pp);
+        if (plain.passes.size() != fused.passes.size()) {
+            std::printf("blocks changed the pass partition\n");
+            return 1;
+        }
+        for (size_t pi = 0; pi < fused.passes.size(); ++pi) {
+            const Pass& pr = plain.passes[pi];
+            const Pass& pf = fused.passes[pi];
+            const int tb = pf.lt + pf.nh;
+            if (tb != 12 || pf.blocks.empty()) continue;
+            std::vector<DevOp> ref_ops;
+            for (const HostOp& ho : pr.ops) ref_ops.push_back(encode_device_op(QT_C128, pr, ho));
+            std::vector<float> blkbuf;
+            std::vector<DevOp> ops;
+            for (const HostOp& ho : pf.ops) ops.push_back(encode_device_op(QT_C128, pf, ho, &blkbuf));
+            for (int reorder = 0; reorder < 2; ++reorder) {
+                DevPass dp;
+                std::memset(&dp, 0, sizeof dp);
+                dp.lt = pf.lt;
+                dp.nh = pf.nh;
+                std::vector<DevOp> planned = ops;
+                plan_register_layout(&dp, &planned, 16, reorder != 0);
+                if (!dp.mma || dp.nreg != 4 || dp.nwarp != 3) {
+                    std::printf("a pass with blocks was not planned for the tensor-core kernel\n");
+                    return 1;
+                }
+                const uint64_t base = rng();
+                std::vector<cd> T(size_t(1) << tb);
+                for (cd& v : T) v = cd(U(rng), U(rng));
+                std::vector<cd> ref = T, got = T;
+                for (const DevOp& o : ref_ops) apply_reference(o, ref, tb, base);
+                run_planned(planned, dp, got, base, &pf.blocks);
+                double err = 0.0;
+                for (size_t j = 0; j < T.size(); ++j) err = std::max(err, std::abs(ref[j] - got[j]));
+                if (!(err <= 1e-12)) {
+                    std::printf("MISMATCH (blocks) circuit %d pass %zu, %zu ops, %zu blocks, reorder %d: max err %.3e\n",
+                                ci, pi, pf.ops.size(), pf.blocks.size(), reorder, err);
+                    return 1;
+                }
+            }
+            ++nblk_passes;
+        }
+    }
+    if (g_blocks == 0) {
+        std::printf("no tensor-core block was planned\n");
+        return 1;
+    }
+    std::printf("OK %ld %ld %ld %ld %ld\n", npasses, nops, g_groups, nblk_passes, g_blocks);
     return 0;
 }

@@ -21,6 +21,19 @@ def built():
     B.load()
 
 
+def state_bytes(circ):
+    return (1 << circ.n) * (8 if circ.dtype == "c64" else 16)
+
+
+def budget_shares(states, budget):
+    """The server's checkpoint budget per circuit (qtask.h, qt_server): the
+    budget less one spare state per circuit, split by state size, at least
+    two states each."""
+    tot = float(sum(states))
+    pool = budget - tot
+    return [int(max(pool * s / tot if pool > 0 else 0.0, 2.0 * s)) for s in states]
+
+
 def mixed_dtype(c):
     return "c64" if c % 2 else "c128df"
 
@@ -48,6 +61,18 @@ def run_scenario(ncirc, nreq, workers, budget, seed, qubits=(9, 14), gates=(60, 
         circ.load_levels([list(lv) for lv in mirrors[c]])
         circ.update_state()
         alone.append((circ, [list(x) for x in ids[c]]))
+    if callable(budget):
+        budget = budget(None, server_c)
+    if budget > 0:
+        # the server gives each circuit this checkpoint budget; the copies
+        # edited alone get the same, and both are brought to its segments
+        # first, so that both plan the same segments (the segment boundaries
+        # decide which gates fuse, and so the rounding)
+        shares = budget_shares([state_bytes(c) for c in server_c], budget)
+        for circ, (acirc, _), share in zip(server_c, alone, shares):
+            for x in (circ, acirc):
+                x.set_option("ckpt_budget", share)
+                x.update_state()
     srv = B.Server(workers=workers, hbm_budget_bytes=budget)
     slots = [srv.add_circuit(circ) for circ in server_c]
     replaced = [set() for _ in range(ncirc)]
@@ -135,10 +160,15 @@ def test_server_at_served_sizes_against_the_oracle():
 
 
 def test_server_budget_evicts_and_stays_correct():
-    # budget for about two circuits' checkpoints: the others are evicted and
-    # re-simulated in full when their turn comes
-    budget = 4 << 20
-    ns, server_c, alone, mirrors, results, info = run_scenario(ncirc=7, nreq=30, workers=2, budget=budget, seed=8)
+    # a budget that holds the three largest circuits with their minimum of
+    # state, one checkpoint and one spare state each, but not all seven: the
+    # others are evicted and re-simulated in full when their turn comes
+    def budget_for(_, circs):
+        sizes = sorted((state_bytes(c) for c in circs), reverse=True)
+        return 3 * sum(sizes[:3])
+    ns, server_c, alone, mirrors, results, info = run_scenario(ncirc=7, nreq=30, workers=2, budget=budget_for,
+                                                               seed=8)
+    budget = budget_for(None, server_c)
     assert all(r["status"] == B.QT_OK for r in results)
     assert info["evictions"] > 0
     assert info["resident_bytes"] <= budget
@@ -147,6 +177,25 @@ def test_server_budget_evicts_and_stays_correct():
         # pending edits re-simulates it in full (a no-op for resident ones)
         circ.update_state()
         assert np.array_equal(circ.read_amplitudes().view(np.uint8), alone[c][0].read_amplitudes().view(np.uint8))
+
+
+def test_server_budget_shares_keep_every_circuit_resident():
+    """A budget that holds every state with a few checkpoints each: the
+    server divides it into checkpoint shares, nothing is evicted, the device
+    bytes stay within the budget, and each circuit's result is bit-identical
+    to the same requests made alone with the same checkpoint share."""
+    def budget_for(_, circs):
+        return 6 * sum(state_bytes(c) for c in circs)
+    ns, server_c, alone, mirrors, results, info = run_scenario(ncirc=7, nreq=40, workers=3, budget=budget_for,
+                                                               seed=12)
+    assert all(r["status"] == B.QT_OK for r in results)
+    assert info["evictions"] == 0
+    assert info["resident_bytes"] <= budget_for(None, server_c)
+    for c, circ in enumerate(server_c):
+        assert np.array_equal(circ.read_amplitudes().view(np.uint8), alone[c][0].read_amplitudes().view(np.uint8)), c
+        want = oracle.simulate(ns[c], W.flatten(mirrors[c]))
+        tol = 1e-5 if circ.dtype == "c64" else 1e-12
+        assert np.max(np.abs(circ.read_amplitudes().astype(np.complex128) - want)) <= tol, c
 
 
 def test_server_rejects_a_circuit_larger_than_the_budget():
