@@ -176,13 +176,33 @@ def make_workload(seed, rounds):
     return levels, model, stream_model, edits
 
 
-# Arithmetic peaks from unit counts and the maximum SM clock: 152 SMs x 128
-# binary32 lanes x 2.07 GHz issue one binary32 instruction each per cycle;
-# binary64 FMA throughput is the measured 593 G/s of this GB300 (about 1.9 per
-# cycle per SM).  Float-float arithmetic is counted in binary32 instructions.
+# Arithmetic peaks from unit counts and the maximum SM clock: SMs (read from
+# the device) x 128 binary32 lanes x the maximum SM clock issue one binary32
+# instruction each per cycle; binary64 FMA throughput is the measured 593 G/s
+# of this GB300 (about 1.9 per cycle per SM of 152).  Float-float arithmetic
+# is counted in binary32 instructions.
 SM_COUNT, SM_MAX_GHZ = 152, 2.07
 FP32_PEAK_TOPS = SM_COUNT * 128 * SM_MAX_GHZ / 1e3
 FP64_PEAK_TOPS = 0.593
+
+
+def set_device_peaks(dev_index=0):
+    """The SM count of the device in use and the maximum SM clock
+    (MEASURED_PEAKS.json's, else the GB300's 2070 MHz) set the binary32
+    issue roof; the binary64 roof scales with the SM count."""
+    global SM_COUNT, SM_MAX_GHZ, FP32_PEAK_TOPS, FP64_PEAK_TOPS
+    try:
+        import torch
+        SM_COUNT = int(torch.cuda.get_device_properties(dev_index).multi_processor_count)
+    except Exception:
+        pass
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            SM_MAX_GHZ = float(json.load(f)["sm_max_mhz"]) / 1e3
+    except Exception:
+        pass
+    FP32_PEAK_TOPS = SM_COUNT * 128 * SM_MAX_GHZ / 1e3
+    FP64_PEAK_TOPS = 0.593 * SM_COUNT / 152
 
 
 def roofline_pair(hbm_achieved, hbm_peak, peak_kind, alu_ops, kern_ms, dtype, traffic, launches, bytes_per_unit):
@@ -196,7 +216,9 @@ def roofline_pair(hbm_achieved, hbm_peak, peak_kind, alu_ops, kern_ms, dtype, tr
     alu = {"bound": "alu", "achieved": alu_ach, "peak": alu_peak,
            "unit": "T binary64 ops/s" if dtype == "c128" else "T binary32 ops/s",
            "frac": (alu_ach / alu_peak) if alu_ach else None,
-           "peak_source": "unit counts x max SM clock" if dtype != "c128" else "measured FP64 FMA rate",
+           "peak_source": (f"unit counts x max SM clock ({SM_COUNT} SMs x 128 lanes x {SM_MAX_GHZ:.2f} GHz)"
+                           if dtype != "c128" else f"measured FP64 FMA rate ({SM_COUNT} SMs)"),
+           "sm_count": SM_COUNT,
            "ops_per_unit": "float-float: 86 binary32 ops per amplitude for a complex 2x2, 38 for a real 2x2, "
                            "diagonal or complex multiply" if dtype == "c128df" else "8 per complex 2x2 row, 4 real/mul"}
     primary = alu if (alu["frac"] or 0) > (hbm["frac"] or 0) else hbm
@@ -229,6 +251,7 @@ def run_ours(args):
     if world > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
     torch.cuda.set_device(local_rank)
+    set_device_peaks(local_rank)
     qbuild.build()
     B.load()
     dev = torch.device("cuda", local_rank)
@@ -422,6 +445,21 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def host_record():
+    """The host cores the oracle runs on: model name (from /proc/cpuinfo or
+    lscpu) and the number of online CPUs."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().lower().startswith("model name"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    return {"cpu_model": model, "nproc": os.cpu_count(), "machine": os.uname().machine}
+
+
 def cpu_baseline(levels, budget_s=15.0, gates_cap=None, n=None, keep=None):
     """The FP64 oracle on the host cores: a prefix of the workload's circuit at
     full size, gate by gate, until the time budget is spent.  With a dict
@@ -444,7 +482,8 @@ def cpu_baseline(levels, budget_s=15.0, gates_cap=None, n=None, keep=None):
     if keep is not None:
         keep.update(psi=psi, gates=gates[:done])
     return {"value": done * (1 << n) / dt, "unit": "amp-updates/s", "cores": nth, "kind": "oracle",
-            "sample": f"first {done} gates of the n={n} circuit, full state, FP64 textbook loops ({dt:.1f} s)"}
+            "sample": f"first {done} gates of the n={n} circuit, full state, FP64 textbook loops ({dt:.1f} s)",
+            "host": host_record()}
 
 
 def oracle_prefix_accuracy(B, W, n, p, dtype, keep, tol):
@@ -688,6 +727,7 @@ def run_deep30(args):
     from paper_2210_01076_gb300 import workloads as W
     qbuild.build()
     B.load()
+    set_device_peaks(0)
     from paper_2210_01076_gb300 import tuning
     n, ngates = args.deep_n, 2000
     p = min(18, n)
@@ -778,38 +818,45 @@ def run_deep30(args):
 def deep30_whole_state_accuracy(B, W, c, n, p, dtype, levels, with_oracle):
     """The final state (after the full simulation and the tail edits) over
     all 2^n amplitudes: a complex64 result against a float-float run of the
-    same gates (on the device); with `with_oracle`, the result against the
-    FP64 oracle's full simulation of the same gates on the host cores
-    (2000 gates on 2^30 amplitudes: minutes on 16 cores, 16 GiB)."""
+    same gates (on the device); with `with_oracle`, the result -- and, for a
+    complex64 run, the float-float reference too -- against the FP64
+    oracle's full simulation of the same gates on the host cores (2000
+    gates on 2^30 amplitudes: minutes on 16 cores, 16 GiB)."""
     out = {}
-    if dtype == "c64":
-        ref = B.Circuit(n, "c128df", p)
-        try:
+    ref = None
+    try:
+        if dtype == "c64":
+            ref = B.Circuit(n, "c128df", p)
             ref.set_option("ckpt_interval", 1 << 20)
             ref.load_levels(levels)
             ref.update_state()
             out["vs_c128df"] = {"max_abs": c.max_abs_diff(ref), "fidelity": c.fidelity(ref),
                                 "tolerance": {"max_abs": 1e-5, "fidelity": 1 - 1e-6}}
-        finally:
+        if with_oracle:
+            import oracle
+            t0 = time.perf_counter()
+            want = oracle.simulate(n, W.flatten(levels), nthreads=oracle.max_threads())
+            t_or = time.perf_counter() - t0
+            sides = [(dtype, c, 1e-5 if dtype == "c64" else 1e-12)]
+            if ref is not None:
+                sides.append(("c128df", ref, 1e-12))
+            for name, circ, tol in sides:
+                err, dot, na, chunk = 0.0, 0j, 0.0, 1 << 24
+                for first in range(0, 1 << n, chunk):
+                    cnt = min(chunk, (1 << n) - first)
+                    a = circ.read_amplitudes(first, cnt).astype(np.complex128)
+                    w = want[first:first + cnt]
+                    err = max(err, float(np.max(np.abs(a - w))))
+                    dot += np.vdot(w, a)
+                    na += float(np.vdot(a, a).real)
+                out[f"{name}_vs_fp64_oracle"] = {"max_abs": err, "fidelity": float(abs(dot) ** 2 / na),
+                                                 "tolerance": tol}
+            out["oracle"] = {"seconds": t_or, "threads": oracle.max_threads(), "gates": len(W.flatten(levels)),
+                             "host": host_record()}
+            del want
+    finally:
+        if ref is not None:
             ref.close()
-    if with_oracle:
-        import oracle
-        t0 = time.perf_counter()
-        want = oracle.simulate(n, W.flatten(levels), nthreads=oracle.max_threads())
-        t_or = time.perf_counter() - t0
-        err, dot, na, chunk = 0.0, 0j, 0.0, 1 << 24
-        for first in range(0, 1 << n, chunk):
-            cnt = min(chunk, (1 << n) - first)
-            a = c.read_amplitudes(first, cnt).astype(np.complex128)
-            w = want[first:first + cnt]
-            err = max(err, float(np.max(np.abs(a - w))))
-            dot += np.vdot(w, a)
-            na += float(np.vdot(a, a).real)
-        out["vs_fp64_oracle"] = {"max_abs": err, "fidelity": float(abs(dot) ** 2 / na),
-                                 "tolerance": 1e-5 if dtype == "c64" else 1e-12,
-                                 "oracle_s": t_or, "oracle_threads": oracle.max_threads(),
-                                 "gates": len(W.flatten(levels))}
-        del want
     return out or None
 
 
@@ -1118,7 +1165,7 @@ def run_reference(args):
         "config": config_dict(world),
         "cpu_baseline": {"value": value, "unit": "amp-updates/s", "cores": nth, "kind": "oracle",
                          "sample": f"{per_step} gates of the n=24 circuit per step (a CPU re-simulation "
-                                   f"re-runs every gate after the edit)"},
+                                   f"re-runs every gate after the edit)", "host": host_record()},
         "e2e": {"value": value, "unit": "amp-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)

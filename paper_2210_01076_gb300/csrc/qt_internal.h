@@ -263,19 +263,27 @@ constexpr int kOpChunk = 64;
 // seven tile bits outside the block, column 2b + {re, im} (64) = block index
 // b.  A thread's amplitude at physical slot (lane, register, warp) has row
 // and block index given by XOR-ing the contributions of its set physical
-// bits and of the pending flip (all linear over GF(2)).  After the op the
-// layout is fixed: lane bit i = row bit i, warp bits 0-1 = row bits 5-6,
-// register bit k = block bit k, warp bit 2 = block bit 4.
+// bits and of the pending flip (all linear over GF(2)); so has its byte
+// offset in the swizzled operand (block_a_offset), whose bit fields (block
+// bit 4; row bits 3-6; row bits 0-2; block bits 1-3 XOR row bits 0-2; block
+// bit 0) sit at disjoint positions.  The op holds those offset
+// contributions.  After the op the layout is fixed: lane bit i = row bit i,
+// warp bits 0-1 = row bits 5-6, register bit k = block bit k, warp bit 2 =
+// block bit 4.
 struct BlockStage {
-    int64_t boff;                  // byte offset of the block's operand B (tf32 hi, then lo; 32 KB)
-    uint8_t m_lane[5], k_lane[5];  // row / block-index bits contributed by each lane-id bit
-    uint8_t m_reg[5], k_reg[5];    // ... by each register-index bit
-    uint8_t m_warp[3], k_warp[3];  // ... by each warp-id bit
-    uint8_t m_flip, k_flip;        // ... by the pending flip
-    int8_t s[5];                   // tile bit of block bit i
-    int8_t rows[7];                // tile bit of row bit i
+    int64_t boff;     // byte offset of the block's operand B (tf32 hi, then lo; 32 KB)
+    int8_t s[5];      // tile bit of block bit i
+    int8_t rows[7];   // tile bit of row bit i
+    uint16_t a_lane[5], a_reg[4], a_warp[3], a_flip;  // operand-A byte-offset contributions
 };
 static_assert(sizeof(BlockStage) <= 64, "BlockStage fits DevOp::m");
+// Byte offset of element (row m, column 2 kb) of the operand-A layout:
+// K-major fp32, two 32-column K atoms of 128 rows x 128 B, 16-byte chunks
+// swizzled by the row's low three bits (XOR-linear in the bits of m and kb).
+constexpr uint32_t block_a_offset(uint32_t m, uint32_t kb) {
+    return ((2u * kb) >> 5) * 16384u + (m >> 3) * 1024u + (m & 7u) * 128u +
+           (((((2u * kb) & 31u) >> 2) ^ (m & 7u)) << 4) + (((2u * kb) & 3u) << 2);
+}
 constexpr int kBlockBytes = 32768;  // operand B of one block: 64 x 64 tf32, hi and lo
 
 struct DevPass {

@@ -428,8 +428,9 @@ struct MmaCtx {
     int* err;
     uint32_t tmem;
     uint32_t ph_b, ph_m;
-    bool pending;  // MMAs issued whose completion has not been seen
+    bool pending;    // MMAs issued whose completion has not been seen
     bool abort;
+    bool tile_read;  // a layout change read the A region since the last barrier
 };
 
 // The tensor-core block op: the tile (in registers, any layout) is written
@@ -449,38 +450,38 @@ __device__ __forceinline__ bool mma_block(typename A::cx (&x)[1 << RB], const De
     static_assert(RB == 4 && sizeof(typename A::amp_t) == 8, "tensor-core blocks: complex64 tiles of 4096");
     constexpr int R = 1 << RB;
     const BlockStage& bs = *reinterpret_cast<const BlockStage*>(&op->m);
-    __syncthreads();  // every thread is done with the A region (layout change) and the accumulator
+    // A layout change since the last barrier may still be reading the A
+    // region (its buffer); the previous block's accumulator reads are
+    // ordered by the barrier before the MMAs are issued.
+    if (mc->tile_read) __syncthreads();
+    mc->tile_read = false;
     if (threadIdx.x == 0) {
         mbar_arrive_expect_tx(mc->bar_b, uint32_t(kBlockBytes));
         const unsigned char* src = mc->blk + bs.boff;
 #pragma unroll
         for (int q = 0; q < 4; ++q) bulk_g2s(mc->b_sm + q * 8192, src + q * 8192, 8192u, mc->bar_b);
     }
-    uint32_t mt = bs.m_flip, kt = bs.k_flip;
+    // byte offset of each register's amplitude in operand A: XOR of the
+    // contributions of the thread's set lane and warp bits, the flip and the
+    // register's set bits
+    uint32_t at = bs.a_flip;
 #pragma unroll
     for (int i = 0; i < 5; ++i)
-        if ((lane >> i) & 1u) {
-            mt ^= bs.m_lane[i];
-            kt ^= bs.k_lane[i];
-        }
+        if ((lane >> i) & 1u) at ^= bs.a_lane[i];
 #pragma unroll
     for (int w = 0; w < 3; ++w)
-        if ((wid >> w) & 1u) {
-            mt ^= bs.m_warp[w];
-            kt ^= bs.k_warp[w];
-        }
+        if ((wid >> w) & 1u) at ^= bs.a_warp[w];
+    uint32_t ar[RB];
+#pragma unroll
+    for (int k = 0; k < RB; ++k) ar[k] = bs.a_reg[k];
     unsigned char* a_hi = mc->a_sm;
     unsigned char* a_lo = mc->a_sm + 32768;
 #pragma unroll
     for (int r = 0; r < R; ++r) {
-        uint32_t m = mt, kb = kt;
+        uint32_t off = at;
 #pragma unroll
         for (int k = 0; k < RB; ++k)
-            if ((r >> k) & 1) {
-                m ^= bs.m_reg[k];
-                kb ^= bs.k_reg[k];
-            }
-        const uint32_t off = tc::sw128_offset(m, 2u * kb, 128u);
+            if ((r >> k) & 1) off ^= ar[k];
         const float rh = tc::to_tf32(x[r].re), ih = tc::to_tf32(x[r].im);
         *reinterpret_cast<float2*>(a_hi + off) = make_float2(rh, ih);
         *reinterpret_cast<float2*>(a_lo + off) =
@@ -569,6 +570,7 @@ __device__ __forceinline__ void run_ops(typename A::cx (&x)[1 << RB], const DevO
             const TileMap<RB> to = tile_map<RB>(nullptr, op->perm, op->perm + RB, op->nwarp, 0u, lane, wid);
 #pragma unroll
             for (int r = 0; r < R; ++r) x[r] = A::ld(tile[to.idx(r)]);
+            if constexpr (MG) mc->tile_read = true;
             continue;
         }
         if constexpr (MG) {
@@ -620,21 +622,40 @@ __device__ __forceinline__ void run_ops(typename A::cx (&x)[1 << RB], const DevO
             if constexpr (PG) {
                 // Merged phases, step by step: a thread multiplies the factors of
                 // the step's terms whose conditions hold for it, then applies the
-                // product to the step's registers.
+                // product to the step's registers.  The conditions outside the
+                // tile are the same for every thread of the CTA: each warp tests
+                // them for 32 terms at once (a ballot) and then walks only the
+                // terms that hold, in order.
                 const int nt = op->b1;
-                for (int i = 0; i < nt; ++i) {
+                const PhTerm* terms = reinterpret_cast<const PhTerm*>(op + 1);
+                uint64_t live = 0;
+                for (int i0 = 0; i0 < nt; i0 += 32) {
+                    const int i = i0 + int(lane);
+                    const bool ok = i < nt && (base & terms[i].cm_glob) == terms[i].cm_glob;
+                    live |= uint64_t(__ballot_sync(0xffffffffu, ok)) << i0;
+                }
+                uint64_t ends;
+                memcpy(&ends, op->perm, sizeof ends);  // bit i: term i ends its step
+                uint64_t rest = nt >= 64 ? ~uint64_t(0) : (uint64_t(1) << nt) - 1;
+                ends |= uint64_t(1) << (nt - 1);  // the group's last term always ends a step
+                // every step clears at least its last term from `rest`: at most nt steps
+                for (int guard = 0; rest && guard < 64; ++guard) {
+                    const int e = __ffsll(static_cast<long long>(ends & rest)) - 1;
+                    const uint64_t step = rest & (e >= 63 ? ~uint64_t(0) : (uint64_t(2) << e) - 1);
+                    uint64_t m = live & step;
                     cx f = A::matp(op, 0);
                     bool go = false;
-                    for (;; ++i) {
-                        const PhTerm& t = reinterpret_cast<const PhTerm*>(op + 1)[i];
-                        if ((base & t.cm_glob) == t.cm_glob && ((threadIdx.x ^ t.cv_thr) & t.cm_thr) == t.cm_thr) {
+                    while (m) {
+                        const int i = __ffsll(static_cast<long long>(m)) - 1;
+                        m &= m - 1;
+                        const PhTerm& t = terms[i];
+                        if (((threadIdx.x ^ t.cv_thr) & t.cm_thr) == t.cm_thr) {
                             f = go ? A::mul(A::coef(t), f) : A::coef(t);
                             go = true;
                         }
-                        if (t.last || i + 1 == nt) break;
                     }
-                    const PhTerm& tl = reinterpret_cast<const PhTerm*>(op + 1)[i];
-                    if (go) RO::apply01(x, tl.mcls, tl.k, [&](cx v) { return A::mul(f, v); });
+                    if (go) RO::apply01(x, terms[e].mcls, terms[e].k, [&](cx v) { return A::mul(f, v); });
+                    rest &= ~step;
                 }
                 oi += (nt + kTermsPerSlot - 1) / kTermsPerSlot;  // the term slots
             }
@@ -695,7 +716,7 @@ __global__ void __launch_bounds__(256, MG ? 2 : reg_min_blocks<A, RB>()) k_pass_
         mc.blk = dp.blk;
         mc.err = err;
         mc.ph_b = mc.ph_m = 0;
-        mc.pending = mc.abort = false;
+        mc.pending = mc.abort = mc.tile_read = false;
         tile = reinterpret_cast<amp_t*>(mc.a_sm);
         if (threadIdx.x == 0) {
             mbar_init(mc.bar_b, 1);

@@ -670,6 +670,12 @@ void emit_group(std::vector<DevOp>* out, const std::vector<const DevOp*>& m, int
     h.b0 = -1;
     h.b1 = int32_t(terms.size());
     h.rh.code = RC_PH_GROUP;
+    // bit i: term i is the last of its step (the kernel walks the steps by it)
+    uint64_t ends = 0;
+    for (size_t i = 0; i < terms.size(); ++i)
+        if (terms[i].last) ends |= uint64_t(1) << i;
+    static_assert(sizeof(h.perm) == sizeof(ends), "step-end mask fits the header's perm field");
+    std::memcpy(h.perm, &ends, sizeof ends);
     out->push_back(h);
     for (size_t i = 0; i < terms.size(); i += kTermsPerSlot) {
         DevOp slot;
@@ -687,7 +693,7 @@ bool merge_phase_groups(std::vector<DevOp>* ops_io, int coef_bytes, int nreg) {
     std::vector<DevOp>& ops = *ops_io;
     const int R = 1 << nreg;
     const PhaseCost cost(coef_bytes);
-    constexpr int kMaxTerms = 15 * kTermsPerSlot;
+    constexpr int kMaxTerms = 15 * kTermsPerSlot;  // 60: the kernel tracks a group's terms in one 64-bit mask
     std::vector<DevOp> out;
     bool any = false;
     size_t i = 0;
@@ -893,29 +899,23 @@ void plan_register_layout(DevPass* dp, std::vector<DevOp>* ops_io, int coef_byte
             if (!done[j] && !commute(i, j)) --npred[j];
         DevOp o = ops[i];
         if (o.kind == OP_BLOCK) {
-            // tensor-core block: record where each physical bit's tile bit goes
-            // (row or block index), then take the fixed post-MMA layout
+            // tensor-core block: record, for each physical bit and the flip,
+            // the operand-A byte offset its tile bit contributes (row or block
+            // index), then take the fixed post-MMA layout
             BlockStage& bs = *reinterpret_cast<BlockStage*>(&o.m);
-            auto contrib = [&](int t, uint8_t* mrow, uint8_t* kblk) {
-                *mrow = 0;
-                *kblk = 0;
+            auto contrib = [&](int t) -> uint16_t {
                 for (int i = 0; i < 5; ++i)
-                    if (bs.s[i] == t) *kblk = uint8_t(1u << i);
+                    if (bs.s[i] == t) return uint16_t(block_a_offset(0u, 1u << i));
                 for (int i = 0; i < 7; ++i)
-                    if (bs.rows[i] == t) *mrow = uint8_t(1u << i);
+                    if (bs.rows[i] == t) return uint16_t(block_a_offset(1u << i, 0u));
+                return 0;
             };
-            for (int b = 0; b < 5; ++b) contrib(L.lane[b], &bs.m_lane[b], &bs.k_lane[b]);
-            for (int k = 0; k < nreg; ++k) contrib(L.reg[k], &bs.m_reg[k], &bs.k_reg[k]);
-            for (int w = 0; w < nwarp; ++w) contrib(L.warp[w], &bs.m_warp[w], &bs.k_warp[w]);
-            bs.m_flip = 0;
-            bs.k_flip = 0;
-            for (int t = 0; t < tb; ++t) {
-                if (!((L.flip >> t) & 1u)) continue;
-                uint8_t mr, kb;
-                contrib(t, &mr, &kb);
-                bs.m_flip ^= mr;
-                bs.k_flip ^= kb;
-            }
+            for (int b = 0; b < 5; ++b) bs.a_lane[b] = contrib(L.lane[b]);
+            for (int k = 0; k < 4; ++k) bs.a_reg[k] = k < nreg ? contrib(L.reg[k]) : 0;
+            for (int w = 0; w < 3; ++w) bs.a_warp[w] = w < nwarp ? contrib(L.warp[w]) : 0;
+            bs.a_flip = 0;
+            for (int t = 0; t < tb; ++t)
+                if ((L.flip >> t) & 1u) bs.a_flip ^= contrib(t);
             std::memset(&L, 0, sizeof L);
             for (int b = 0; b < 5; ++b) L.lane[b] = bs.rows[b];
             for (int k = 0; k < 4; ++k) L.reg[k] = bs.s[k];

@@ -104,12 +104,5 @@ __device__ __forceinline__ float to_tf32(float x) {
     return __uint_as_float(r);
 }
 
-// Byte offset of element (row, k) of a K-major, 128-byte-swizzled fp32
-// operand with `rows` rows and K = 64 (two 32-element K atoms).
-__device__ __forceinline__ uint32_t sw128_offset(uint32_t row, uint32_t k, uint32_t rows) {
-    return (k >> 5) * (rows * 128u) + (row >> 3) * 1024u + (row & 7u) * 128u + ((((k & 31u) >> 2) ^ (row & 7u)) << 4) +
-           ((k & 3u) << 2);
-}
-
 }  // namespace tc
 }  // namespace qt

@@ -171,13 +171,20 @@ static void run_planned(const std::vector<DevOp>& ops, const DevPass& dp, std::v
             for (int w = 0; w < P.W; ++w)
                 for (int r = 0; r < P.R; ++r)
                     for (int l = 0; l < 32; ++l) {
-                        uint32_t m = bs.m_flip, kb = bs.k_flip;
+                        uint32_t a = bs.a_flip;
                         for (int i = 0; i < 5; ++i)
-                            if ((l >> i) & 1) m ^= bs.m_lane[i], kb ^= bs.k_lane[i];
+                            if ((l >> i) & 1) a ^= bs.a_lane[i];
                         for (int k = 0; k < P.nreg; ++k)
-                            if ((r >> k) & 1) m ^= bs.m_reg[k], kb ^= bs.k_reg[k];
+                            if ((r >> k) & 1) a ^= bs.a_reg[k];
                         for (int k = 0; k < P.nwarp; ++k)
-                            if ((w >> k) & 1) m ^= bs.m_warp[k], kb ^= bs.k_warp[k];
+                            if ((w >> k) & 1) a ^= bs.a_warp[k];
+                        // decode the swizzled operand-A byte offset into (row, block index)
+                        const uint32_t m = ((a >> 10) & 15u) << 3 | ((a >> 7) & 7u);
+                        const uint32_t kb = ((a >> 14) & 1u) << 4 | ((((a >> 4) & 7u) ^ (m & 7u)) << 1) | ((a >> 3) & 1u);
+                        if (block_a_offset(m, kb) != a) {
+                            std::printf("operand offset %u is not a (row, block index) position\n", a);
+                            std::exit(1);
+                        }
                         Am[m * 32 + kb] = P.at(l, r, w);
                     }
             for (int m = 0; m < 128; ++m)
