@@ -79,7 +79,7 @@ def measured_peak():
 
 def kernel_source_hash():
     h = hashlib.sha256()
-    for f in ("qt_kernels.cu", "qt_pass_reg.cu", "qt_arith.cuh", "qt_internal.h"):
+    for f in ("qt_kernels.cu", "qt_pass_reg.cu", "qt_arith.cuh", "qt_internal.h", "qt_tc.cuh", "qt_launch.cuh"):
         with open(os.path.join(ROOT, "paper_2210_01076_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -595,6 +595,13 @@ def config3_block(B, W, peak, peak_kind):
             bpa = 8 if dt == "c64" else 16
             kb, km = full["pass_kernel_bytes"], full["pass_kernel_ms"]
             achieved = kb / (km * 1e-3) / 1e9 if km > 0 else None
+            traffic = None
+            t = profiled_traffic(kernel_source_hash(), "k_pass_c64_traffic.json" if dt == "c64" else
+                                 "k_pass_df_traffic.json")
+            if t and full["pass_kernel_launches"]:
+                # ncu DRAM bytes per amplitude-pass (a smaller capture of the
+                # same kernel), scaled to this run's average launch
+                traffic = t["dram_bytes_per_amp_pass"] * (kb / (2 * bpa)) / full["pass_kernel_launches"]
             out[dt].update({
                 "full_sim_ms": full["gpu_ms"], "amp_updates_per_s": full["amp_updates"] / (full["gpu_ms"] * 1e-3),
                 "hbm_gbs": full["hbm_bytes"] / (full["gpu_ms"] * 1e-3) / 1e9,
@@ -602,8 +609,10 @@ def config3_block(B, W, peak, peak_kind):
                 "incremental_ms": {"p50": pctl([x["gpu_ms"] for x in inc], 50),
                                    "p99": pctl([x["gpu_ms"] for x in inc], 99)},
                 "clean_fraction_mean": float(np.mean([x["clean_fraction"] for x in inc])),
-                "roofline": roofline_pair(achieved, peak, peak_kind, full["pass_kernel_alu_ops"], km, dt, None,
+                "roofline": roofline_pair(achieved, peak, peak_kind, full["pass_kernel_alu_ops"], km, dt, traffic,
                                           full["pass_kernel_launches"], f"{2 * bpa} B per amplitude per pass")})
+            if dt == "c64":
+                out["c64_tensor_blocks"] = _guard(config3_tensor_blocks, B, W, base, c, full["gpu_ms"])
         c64, df = kept["c64"], kept["c128df"]
         out["c64"]["accuracy"] = {
             "max_abs_vs_c128df_whole_state": c64.max_abs_diff(df), "fidelity_vs_c128df": c64.fidelity(df),
@@ -617,6 +626,33 @@ def config3_block(B, W, peak, peak_kind):
         for c in kept.values():
             c.close()
     return out
+
+
+def config3_tensor_blocks(B, W, base, c64_ref, ref_ms, threshold=60):
+    """The same complex64 circuit with runs of gates on five tile qubits
+    folded into tensor-core blocks (tcgen05, 3xTF32) where the register
+    kernel's estimate for the run exceeds `threshold` tenths of a dense op:
+    full-simulation time against the register-only run, blocks launched,
+    and the largest amplitude difference from the register-only state."""
+    n, p = 30, 18
+    levels = [list(x) for x in base]
+    c = B.Circuit(n, "c64", p)
+    try:
+        c.set_option("tile_high", 5)
+        c.set_option("ckpt_budget", int(64e9))
+        c.set_option("tc_blocks", 1)
+        c.set_option("tc_threshold", threshold)
+        ids = c.load_levels(levels)
+        c.update_state()
+        c.set_option("kernel_timing", 1)  # as the register-only run was timed
+        full = c.update_state(force_full=True)
+        c.set_option("kernel_timing", 0)
+        _tail_edits(B, W, c, ids, levels, 5, seed=11)
+        return {"tc_threshold_tenths": threshold, "full_sim_ms": full["gpu_ms"],
+                "register_only_full_sim_ms": ref_ms, "tensor_blocks_per_full_sim": full["tensor_blocks"],
+                "max_abs_vs_register_path": c.max_abs_diff(c64_ref)}
+    finally:
+        c.close()
 
 
 def config4_block(B, W):

@@ -111,7 +111,7 @@ typedef struct {
     double gpu_ms;               /* device time of the call's stream work (CUDA events), -1 if not timed */
     double pass_kernel_ms;       /* summed device time of the fused-pass kernels (option kernel_timing) or -1 */
     int32_t pass_kernel_launches;
-    int32_t reserved;
+    int32_t tensor_blocks;       /* tensor-core block ops in the launched passes (complex64, option tc_blocks) */
     uint64_t pass_kernel_bytes;  /* algorithmic bytes of those launches */
     uint64_t h2d_bytes;          /* host-to-device bytes uploaded (fused ops and worklists) */
     uint64_t pass_kernel_alu_ops; /* algorithmic floating-point ops of the timed fused-pass launches

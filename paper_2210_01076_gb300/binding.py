@@ -38,7 +38,7 @@ class qt_update_stats(ctypes.Structure):
                 ("partition_passes_run", ctypes.c_int64), ("clean_fraction", ctypes.c_double),
                 ("amp_updates", ctypes.c_uint64), ("hbm_bytes", ctypes.c_uint64), ("host_ms", ctypes.c_double),
                 ("gpu_ms", ctypes.c_double), ("pass_kernel_ms", ctypes.c_double),
-                ("pass_kernel_launches", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("pass_kernel_launches", ctypes.c_int32), ("tensor_blocks", ctypes.c_int32),
                 ("pass_kernel_bytes", ctypes.c_uint64), ("h2d_bytes", ctypes.c_uint64),
                 ("pass_kernel_alu_ops", ctypes.c_uint64)]
 

@@ -56,6 +56,7 @@ struct Launch {
     uint64_t parts_processed;
     int ngates;
     double alu_per_amp;  // algorithmic arithmetic ops per amplitude of the pass
+    int nblocks;         // tensor-core block ops of the pass
 };
 
 // Floating-point operations per amplitude that an op's arithmetic needs (the
@@ -603,6 +604,7 @@ qt_status do_update(qt_circuit* c, int force_full, qt_update_stats* stats) {
             ln.parts_processed = uint64_t(ln.ngroups) << __builtin_popcount(ps.M);
             ln.alu_per_amp = 0.0;
             for (const HostOp& o : ps.ops) ln.alu_per_amp += op_alu_per_amp(c->dtype, o);
+            ln.nblocks = int(ps.blocks.size());
             DevPass& dp = ln.dp;
             std::memset(&dp, 0, sizeof dp);
             dp.p = c->p;
@@ -644,6 +646,7 @@ qt_status do_update(qt_circuit* c, int force_full, qt_update_stats* stats) {
         if (ln.kind == 0) {
             st.passes_run += 1;
             st.partition_passes_run += int64_t(ln.parts_processed);
+            st.tensor_blocks += ln.nblocks;
         }
         st.hbm_bytes += 2 * bpa * ln.parts_processed * part_amps;
     }
