@@ -2,7 +2,7 @@
 
 Workload (one GPU): n = 24 qubits, complex128 amplitudes (float-float
 arithmetic, QT_C128_DF), 1000 random gates (~40 % multi-qubit) in ASAP levels,
-partitions of 2^16 amplitudes, a checkpoint every 4 levels.  A *step* is one
+partitions of 2^16 amplitudes, a checkpoint every 8 levels.  A *step* is one
 incremental round: 1-5 random edits (insert / remove / replace at uniformly
 random levels) followed by qt_update_state -- every row of the hot path
 (circuit store, planning and fusion, dirty tracking, checkpoint restart, the
@@ -35,7 +35,7 @@ sys.path.insert(0, ROOT)
 N_QUBITS = 24
 N_GATES = 1000
 LOG2_PART = 16
-CKPT = 4
+CKPT = 8  # levels per checkpoint segment: the measured best p50 round latency (4..24 swept)
 P_MULTI = 0.4
 SEED = 2210
 WORKLOAD = "incremental random circuit n=24, 1000 gates (~40% multi-qubit), 1-5 edits/round, partitions 2^16"
@@ -232,7 +232,7 @@ def roofline_pair(hbm_achieved, hbm_peak, peak_kind, alu_ops, kern_ms, dtype, tr
 def config_dict(world):
     return {"workload": WORKLOAD, "n_qubits": N_QUBITS, "gates": N_GATES, "log2_partition": LOG2_PART,
             "ckpt_interval_levels": CKPT, "edits_per_round": "1-5", "parallelism": f"replicas{world}",
-            "l2": "inputs larger than L2: state 256 MiB, checkpoints ~9.5 GiB; no flush"}
+            "l2": "inputs larger than L2: state 256 MiB, checkpoints ~5 GiB; no flush"}
 
 
 def pctl(xs, q):
@@ -706,7 +706,7 @@ def config4_block(B, W):
 
 def ieee_c128_block(B, W, levels):
     """IEEE binary64 (QT_C128) on the incremental workload's circuit (n = 24,
-    1000 gates, partitions 2^16, checkpoints every 4 levels): full
+    1000 gates, partitions 2^16, checkpoints every 8 levels): full
     re-simulation time against the float-float path of the same circuit,
     with the fused pass against the binary64 FMA roof."""
     out = {"workload": "incremental workload's circuit, full re-simulation"}

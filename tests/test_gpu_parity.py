@@ -361,5 +361,5 @@ def test_config2_full_size_parity_and_bit_identity():
     multi-threaded oracle, then three edit rounds, each incremental result
     bit-identical to a full re-simulation."""
     n, p = 24, 16
-    cleans = run_edit_stream(n, p, "c128df", 1000, rounds=3, seed=2210, G=4, check_oracle_every=3)
+    cleans = run_edit_stream(n, p, "c128df", 1000, rounds=3, seed=2210, G=8, check_oracle_every=3)
     assert len(cleans) == 3
