@@ -731,6 +731,38 @@ def ieee_c128_block(B, W, levels):
     return out
 
 
+def precision_block(B, W):
+    """The complex64 precision policy on two circuits: a 24-qubit QFT-like
+    circuit of 2000 gates (amplitudes ~2^-12: the complex64 error stays far
+    inside the contract) and a 5-qubit circuit of 50 000 random gates
+    (amplitudes ~0.2: binary32 rounding carries the error past half the
+    max-abs tolerance).  For each: the dtype the policy ends in, the error it
+    measured against the float-float shadow, and the final error against
+    the FP64 oracle over the whole state."""
+    import oracle
+    from paper_2210_01076_gb300.precision import AdaptiveCircuit
+    out = {}
+    for name, n, levels in (("qft_like_n24_2000", 24, W.qft_like_circuit(24, 2000, seed=7)),
+                            ("random_n5_50000", 5, W.random_circuit(5, 50000, seed=5, p_multi=0.4))):
+        ac = AdaptiveCircuit(n, min(n, 16), ckpt_interval=1 << 20)
+        try:
+            ac.load_levels(levels)
+            t0 = time.perf_counter()
+            ac.update_state()
+            dt = time.perf_counter() - t0
+            got = ac.read_amplitudes().astype(np.complex128)
+            want = oracle.simulate(n, W.flatten(levels), nthreads=oracle.max_threads())
+            rec = ac.error.get("switched_from_c64", ac.error)
+            out[name] = {"final_dtype": ac.dtype, "switched": ac.switched_at_update is not None,
+                         "measured_c64_max_abs": rec.get("max_abs"), "measured_c64_infidelity": rec.get("infidelity"),
+                         "final_max_abs_err_vs_fp64_oracle": float(np.max(np.abs(got - want))),
+                         "update_with_check_s": dt}
+        finally:
+            ac.close()
+    out["policy"] = "switch to float-float complex128 when the measured complex64 error exceeds half of 1e-5 max-abs or 1e-6 infidelity"
+    return out
+
+
 def run_configs(args, levels):
     from paper_2210_01076_gb300 import binding as B
     from paper_2210_01076_gb300 import workloads as W
@@ -741,6 +773,7 @@ def run_configs(args, levels):
     out["ieee_binary64_n24"] = _guard(ieee_c128_block, B, W, levels)
     out["deep_qft_n30"] = _guard(config3_block, B, W, peak, peak_kind)
     out["batch256"] = _guard(config4_block, B, W)
+    out["precision_policy"] = _guard(precision_block, B, W)
     if args.configs_serve:
         sargs = argparse.Namespace(**vars(args))
         sargs.serve_seconds, sargs.serve_burst, sargs.serve_check = 1.0, 100, 0
