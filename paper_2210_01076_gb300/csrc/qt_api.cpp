@@ -623,7 +623,10 @@ qt_status do_update(qt_circuit* c, int force_full, qt_update_stats* stats) {
             std::vector<DevOp> pops;
             pops.reserve(ps.ops.size());
             for (const HostOp& o : ps.ops) pops.push_back(encode_op(c->dtype, ps, o, &hblk));
-            if (c->reg_kernel) plan_register_layout(&dp, &pops, int(bytes_per_amp(c->dtype)));
+            if (c->reg_kernel) {
+                plan_register_layout(&dp, &pops, int(bytes_per_amp(c->dtype)));
+                if (dp.reg_kernel) set_register_offsets(&dp);
+            }
             dp.tma = (dp.reg_kernel && c->tma) ? 1 : 0;
             dp.test_stall = c->test_stall ? 1 : 0;
             dp.nops = int32_t(pops.size());

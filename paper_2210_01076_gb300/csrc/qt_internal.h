@@ -13,6 +13,7 @@ namespace qt {
 
 constexpr int kMaxQubits = 34;
 constexpr int kMaxTileHigh = 7;      // tile qubits above the contiguous low run
+constexpr int kMaxRegBits = 5;       // register-index bits of the register kernel (32 amplitudes a thread)
 constexpr int kThreads = 256;        // threads per fused-pass CTA
 
 // ------------------------------------------------------------------ ops --
@@ -308,6 +309,11 @@ struct DevPass {
     int32_t mma;           // 1: the ops hold tensor-core blocks (RC_MMA)
     int32_t pad_mma;
     const unsigned char* blk;  // device buffer of the blocks' B operands (mma passes)
+    // register kernel: amplitude-index offset of each register bit's tile bit
+    // in the initial layout (rin) and the final layout (rout); an amplitude's
+    // index is the thread's index XOR the offsets of its register-index bits
+    uint64_t rin[kMaxRegBits];
+    uint64_t rout[kMaxRegBits];
 };
 
 // Register-kernel layout planning for one pass (host): fills the initial
@@ -321,6 +327,9 @@ struct DevPass {
 // estimated to save work (sets dp->groups).
 void plan_register_layout(DevPass* dp, std::vector<DevOp>* ops, int coef_bytes, bool reorder = true,
                           bool phase_groups = true);
+
+// Fill dp->rin / dp->rout from the planned layouts (needs lt and h).
+void set_register_offsets(DevPass* dp);
 
 // Kernel launchers (qt_kernels.cu).  Return a cudaError_t as int.
 // err: device int set to 1 when a bounded wait of the TMA-staged kernel

@@ -327,6 +327,16 @@ struct TileMap {
     }
 };
 
+// XOR of the amplitude-index offsets of the register-index bits of r
+template <int RB>
+__device__ __forceinline__ uint64_t reg_offset(const uint64_t (&off)[kMaxRegBits], int r) {
+    uint64_t o = 0;
+#pragma unroll
+    for (int k = 0; k < RB; ++k)
+        if ((r >> k) & 1) o ^= off[k];
+    return o;
+}
+
 // lanes == nullptr: lane bit i holds tile bit i.
 template <int RB, class T>
 __device__ __forceinline__ TileMap<RB> tile_map(const int8_t* lanes, const T* regs, const T* warps, int nwarp,
@@ -542,9 +552,11 @@ __device__ __forceinline__ void run_ops(typename A::cx (&x)[1 << RB], const DevO
     // The ops are staged in shared memory, a chunk at a time: every thread
     // reads every op, and a shared-memory broadcast keeps that off the
     // critical path that a global load would be on.  Each op's header (its
-    // dispatch code, bits and conditions, resolved on the host) is one
-    // 16-byte load; the dispatch is a short if-chain by op class (measured
-    // faster than a jump table, and than loading the next header early).
+    // dispatch code, bits and conditions, resolved on the host) is read field
+    // by field where it is used; the dispatch is a short tree of comparisons over ranges
+    // of codes (measured faster than a jump table, and than loading the next
+    // header early), and only the classes that can carry conditions (X,
+    // SWAP, phases) test them.
     __shared__ __align__(16) DevOp s_ops[kOpChunk];
     for (int c0 = 0; c0 < nops; c0 += kOpChunk) {
     const int cn = nops - c0 < kOpChunk ? nops - c0 : kOpChunk;
@@ -558,52 +570,70 @@ __device__ __forceinline__ void run_ops(typename A::cx (&x)[1 << RB], const DevO
     __syncthreads();
     for (int oi = 0; oi < cn; ++oi) {
         const DevOp* op = s_ops + oi;
-        const RegHdr h = op->rh;
-        const uint64_t cmg = op->cm_glob;
-        if (h.code == RC_PERM) {
-            const TileMap<RB> from =
-                layout_map<RB>(*reinterpret_cast<const TileLayout*>(&op->m), op->nwarp, lane, wid);
-            __syncthreads();  // the previous layout change has been read by all
+        // header fields are read from shared memory where they are used
+        const RegHdr& h = op->rh;
+        const int code = h.code;
+        if (code <= RC_X_L) {  // layout change, pair ops, X
+            if (code == RC_PERM) {
+                const TileMap<RB> from =
+                    layout_map<RB>(*reinterpret_cast<const TileLayout*>(&op->m), op->nwarp, lane, wid);
+                __syncthreads();  // the previous layout change has been read by all
 #pragma unroll
-            for (int r = 0; r < R; ++r) tile[from.idx(r)] = A::st(x[r]);
-            __syncthreads();
-            const TileMap<RB> to = tile_map<RB>(nullptr, op->perm, op->perm + RB, op->nwarp, 0u, lane, wid);
+                for (int r = 0; r < R; ++r) tile[from.idx(r)] = A::st(x[r]);
+                __syncthreads();
+                const TileMap<RB> to = tile_map<RB>(nullptr, op->perm, op->perm + RB, op->nwarp, 0u, lane, wid);
 #pragma unroll
-            for (int r = 0; r < R; ++r) x[r] = A::ld(tile[to.idx(r)]);
-            if constexpr (MG) mc->tile_read = true;
-            continue;
-        }
-        if constexpr (MG) {
-            if (h.code == RC_MMA) {
-                if (!mma_block<A, RB>(x, op, lane, wid, mc)) return;
+                for (int r = 0; r < R; ++r) x[r] = A::ld(tile[to.idx(r)]);
+                if constexpr (MG) mc->tile_read = true;
                 continue;
             }
-        }
-        if (h.ren > 0) {
-            // target on register bit ren: bring it to register bit 0 (the
-            // host tracks the same exchange; it happens even when the op is
-            // skipped below, so the layout stays in step)
-            dispatch_k<RB>(h.ren, [&](auto kc) {
-                if constexpr (decltype(kc)::value > 0) RO::template swap_bits<decltype(kc)::value>(x);
-            });
-        }
-        if ((base & cmg) != cmg) continue;  // a control outside the tile is 0: uniform skip
-        const bool thr_ok = ((threadIdx.x ^ h.cv_thr) & h.cm_thr) == h.cm_thr;
-        const uint32_t cmr = h.cm_reg, cvr = h.cv_reg;
-        const int code = h.code;
-        if (code <= RC_IREAL_L) {
-            if (code == RC_DENSE_R) RO::template pair_reg0<OP_DENSE>(x, op);
-            else if (code == RC_DENSE_L) RO::template pair_lane<OP_DENSE>(x, op, h.a, lane);
-            else if (code == RC_REAL_R) RO::template pair_reg0<OP_REAL>(x, op);
-            else if (code == RC_REAL_L) RO::template pair_lane<OP_REAL>(x, op, h.a, lane);
-            else if (code == RC_ANTI_R) RO::template pair_reg0<OP_ANTI>(x, op);
-            else if (code == RC_ANTI_L) RO::template pair_lane<OP_ANTI>(x, op, h.a, lane);
-            else if (code == RC_IREAL_R) RO::template pair_reg0<OP_IREAL>(x, op);
-            else RO::template pair_lane<OP_IREAL>(x, op, h.a, lane);
-        } else if (code <= RC_SWAP_LL) {
+            const int ren = h.ren;
+            if (ren > 0) {
+                // target on register bit ren: bring it to register bit 0 (the
+                // host tracks the same exchange; it happens even when the op is
+                // skipped below, so the layout stays in step)
+                dispatch_k<RB>(ren, [&](auto kc) {
+                    if constexpr (decltype(kc)::value > 0) RO::template swap_bits<decltype(kc)::value>(x);
+                });
+            }
+            if (code <= RC_IREAL_L) {
+                // DENSE, REAL, ANTI and IREAL ops carry no conditions (only
+                // X, SWAP and phases do; the planner's emulator checks it):
+                // no condition tests.  Odd codes are the register-bit
+                // variants.
+                if (code & 1) {
+                    if (code < RC_ANTI_R) {
+                        if (code == RC_DENSE_R) RO::template pair_reg0<OP_DENSE>(x, op);
+                        else RO::template pair_reg0<OP_REAL>(x, op);
+                    } else {
+                        if (code == RC_ANTI_R) RO::template pair_reg0<OP_ANTI>(x, op);
+                        else RO::template pair_reg0<OP_IREAL>(x, op);
+                    }
+                } else {
+                    if (code < RC_ANTI_L) {
+                        if (code == RC_DENSE_L) RO::template pair_lane<OP_DENSE>(x, op, h.a, lane);
+                        else RO::template pair_lane<OP_REAL>(x, op, h.a, lane);
+                    } else {
+                        if (code == RC_ANTI_L) RO::template pair_lane<OP_ANTI>(x, op, h.a, lane);
+                        else RO::template pair_lane<OP_IREAL>(x, op, h.a, lane);
+                    }
+                }
+                continue;
+            }
+            const uint64_t cmg = op->cm_glob;
+            if ((base & cmg) != cmg) continue;  // a control outside the tile is 0: uniform skip
+            const bool thr_ok = ((threadIdx.x ^ h.cv_thr) & h.cm_thr) == h.cm_thr;
+            const uint32_t cmr = h.cm_reg, cvr = h.cv_reg;
             if (code == RC_X_R) RO::x_reg0(x, thr_ok, cmr, cvr);
-            else if (code == RC_X_L) RO::x_lane(x, h.a, thr_ok, cmr, cvr);
-            else if (code == RC_SWAP_LL) RO::swap_ll(x, h.a, h.b, lane, thr_ok, cmr, cvr);
+            else RO::x_lane(x, h.a, thr_ok, cmr, cvr);
+            continue;
+        }
+        if (code <= RC_SWAP_LL) {
+            const uint64_t cmg = op->cm_glob;
+            if ((base & cmg) != cmg) continue;
+            const bool thr_ok = ((threadIdx.x ^ h.cv_thr) & h.cm_thr) == h.cm_thr;
+            const uint32_t cmr = h.cm_reg, cvr = h.cv_reg;
+            if (code == RC_SWAP_LL) RO::swap_ll(x, h.a, h.b, lane, thr_ok, cmr, cvr);
             else if (code == RC_SWAP_LR)
                 dispatch_k<RB>(h.b, [&](auto kc) {
                     RO::template swap_lr<decltype(kc)::value>(x, h.a, lane, thr_ok, cmr, cvr);
@@ -615,10 +645,27 @@ __device__ __forceinline__ void run_ops(typename A::cx (&x)[1 << RB], const DevO
                         if constexpr (K0 < K1) RO::template swap_rr<K0, K1>(x, thr_ok, cmr, cvr);
                     });
                 });
-        } else if (code <= RC_DIAG_R) {
+            continue;
+        }
+        if (code <= RC_DIAG_R) {  // diagonals carry no conditions
             if (code == RC_DIAG_R) RO::diag_r(x, op, h.a);
             else RO::diag_u(x, op, code == RC_DIAG_G ? int((base >> h.a) & 1u) : int((threadIdx.x >> h.a) & 1u));
-        } else if (PG && code == RC_PH_GROUP) {
+            continue;
+        }
+        if constexpr (MG) {
+            if (code == RC_MMA) {
+                if (!mma_block<A, RB>(x, op, lane, wid, mc)) return;
+                continue;
+            }
+        }
+        {
+            const uint64_t cmg = op->cm_glob;
+            if ((base & cmg) != cmg) continue;
+        }
+        const bool thr_ok = ((threadIdx.x ^ h.cv_thr) & h.cm_thr) == h.cm_thr;
+        const uint32_t cmr = h.cm_reg, cvr = h.cv_reg;
+        const int mcls = h.mcls;
+        if (PG && code == RC_PH_GROUP) {
             if constexpr (PG) {
                 // Merged phases, step by step: a thread multiplies the factors of
                 // the step's terms whose conditions hold for it, then applies the
@@ -660,12 +707,12 @@ __device__ __forceinline__ void run_ops(typename A::cx (&x)[1 << RB], const DevO
                 oi += (nt + kTermsPerSlot - 1) / kTermsPerSlot;  // the term slots
             }
         } else if (thr_ok) {
-            if (code == RC_PH_NEG) RO::masked(x, h.mcls, h.a, cmr, cvr, [](cx v) { return A::neg(v); });
-            else if (code == RC_PH_POS_I) RO::masked(x, h.mcls, h.a, cmr, cvr, [](cx v) { return A::mul_i(v); });
-            else if (code == RC_PH_NEG_I) RO::masked(x, h.mcls, h.a, cmr, cvr, [](cx v) { return A::mul_negi(v); });
+            if (code == RC_PH_NEG) RO::masked(x, mcls, h.a, cmr, cvr, [](cx v) { return A::neg(v); });
+            else if (code == RC_PH_POS_I) RO::masked(x, mcls, h.a, cmr, cvr, [](cx v) { return A::mul_i(v); });
+            else if (code == RC_PH_NEG_I) RO::masked(x, mcls, h.a, cmr, cvr, [](cx v) { return A::mul_negi(v); });
             else if (code == RC_PH_GEN) {
                 const cx f = A::matp(op, 0);
-                RO::masked(x, h.mcls, h.a, cmr, cvr, [&](cx v) { return A::mul(f, v); });
+                RO::masked(x, mcls, h.a, cmr, cvr, [&](cx v) { return A::mul(f, v); });
             }
         }
     }
@@ -736,14 +783,17 @@ __global__ void __launch_bounds__(256, MG ? 2 : reg_min_blocks<A, RB>()) k_pass_
     chunk_offsets(dp, choff);
     __syncthreads();
     const uint32_t lowmask = (1u << dp.lt) - 1u;
+    // The amplitude index of tile index j is base | (j & lowmask) |
+    // choff[j >> lt]: XOR-linear in j, with the base's bits disjoint from the
+    // image.  A thread's register r holds tile index thr ^ (register bits of
+    // r), so its amplitude index is the index of thr XOR the offsets of r's
+    // register bits (dp.rin / dp.rout, from the host).
     cx x[R];
     {
         const TileMap<RB> m = initial_map<RB>(dp, lane, wid);
+        const uint64_t g = base | choff[m.thr >> dp.lt] | (m.thr & lowmask);
 #pragma unroll
-        for (int r = 0; r < R; ++r) {
-            const uint32_t j = m.idx(r);
-            x[r] = A::ld(src[base | choff[j >> dp.lt] | (j & lowmask)]);
-        }
+        for (int r = 0; r < R; ++r) x[r] = A::ld(src[g ^ reg_offset<RB>(dp.rin, r)]);
     }
     run_ops<A, RB, PG, MG>(x, ops + dp.op_offset, dp.nops, base, lane, wid, tile, &mc);
     // A pass whose gates were all relabels has no ops, so no barrier has
@@ -752,11 +802,9 @@ __global__ void __launch_bounds__(256, MG ? 2 : reg_min_blocks<A, RB>()) k_pass_
     if (dp.nops == 0) __syncthreads();
     if (!MG || !mc.abort) {
         const TileMap<RB> m = layout_map<RB>(dp.fin, dp.nwarp, lane, wid);
+        const uint64_t g = base | choff[m.thr >> dp.lt] | (m.thr & lowmask);
 #pragma unroll
-        for (int r = 0; r < R; ++r) {
-            const uint32_t j = m.idx(r);
-            dst[base | choff[j >> dp.lt] | (j & lowmask)] = A::st(x[r]);
-        }
+        for (int r = 0; r < R; ++r) dst[g ^ reg_offset<RB>(dp.rout, r)] = A::st(x[r]);
     }
     if constexpr (MG) {
         // an aborted block may still have MMAs in flight: wait for them

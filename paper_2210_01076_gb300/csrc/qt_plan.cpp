@@ -763,6 +763,15 @@ bool merge_phase_groups(std::vector<DevOp>* ops_io, int coef_bytes, int nreg) {
 //  - every other op is resolved against the current layout: targets and
 //    conditions become physical bits, a flipped target exchanges the op's
 //    matrix entries (X U X), a flipped condition is marked in the value mask.
+void set_register_offsets(DevPass* dp) {
+    // tile bit b < lt is amplitude-index bit b; tile bit lt + k is qubit h[k]
+    auto off = [dp](int b) -> uint64_t { return uint64_t(1) << (b < dp->lt ? b : dp->h[b - dp->lt]); };
+    for (int k = 0; k < kMaxRegBits; ++k) {
+        dp->rin[k] = k < dp->nreg ? off(dp->layout[k]) : 0;
+        dp->rout[k] = k < dp->nreg ? off(dp->fin.reg[k]) : 0;
+    }
+}
+
 void plan_register_layout(DevPass* dp, std::vector<DevOp>* ops_io, int coef_bytes, bool reorder, bool phase_groups) {
     const int tb = dp->lt + dp->nh;
     dp->reg_kernel = 0;

@@ -14,7 +14,9 @@
 // results must agree to rounding.  A second part plans complex64-shaped
 // passes (tiles of 12 qubits) with tensor-core blocks and checks the fused
 // blocks (their FP64 matrices, the ops moved ahead of them, the staging
-// masks and the layout after each block) the same way.  This pins the planner's bookkeeping on the
+// masks and the layout after each block) the same way.  Each pass's register
+// offsets (the kernel's amplitude addressing) are checked against the layout
+// index of every position.  This pins the planner's bookkeeping on the
 // CPU; the GPU parity tests pin the kernels against the oracle.
 //
 // Build: g++ -O1 -std=c++17 -I<include> -I<csrc> -I<cuda include>
@@ -105,6 +107,41 @@ static uint32_t layout_index(const int8_t* lane, const int8_t* reg, const int8_t
     for (int k = 0; k < nwarp; ++k)
         if ((w >> k) & 1) j |= 1u << warp[k];
     return j ^ flip;
+}
+
+// The kernel addresses register r of a thread as the amplitude index of the
+// thread's tile index XOR the offsets of r's register bits (set_register_offsets);
+// check that against the index of every (lane, register, warp) position, for
+// the initial and the final layout.
+static bool check_register_offsets(const DevPass& dp) {
+    const uint32_t lowmask = (1u << dp.lt) - 1u;
+    auto gidx = [&](uint32_t j) {
+        uint64_t g = j & lowmask;
+        for (int k = 0; k < dp.nh; ++k)
+            if ((j >> (dp.lt + k)) & 1u) g |= uint64_t(1) << dp.h[k];
+        return g;
+    };
+    int8_t reg0[8], warp0[8];
+    for (int k = 0; k < dp.nreg; ++k) reg0[k] = int8_t(dp.layout[k]);
+    for (int w = 0; w < dp.nwarp; ++w) warp0[w] = int8_t(dp.layout[dp.nreg + w]);
+    for (int side = 0; side < 2; ++side) {
+        const int8_t* ln = side ? dp.fin.lane : nullptr;
+        const int8_t* rg = side ? dp.fin.reg : reg0;
+        const int8_t* wp = side ? dp.fin.warp : warp0;
+        const uint32_t flip = side ? dp.fin.flip : 0u;
+        const uint64_t* off = side ? dp.rout : dp.rin;
+        for (int w = 0; w < (1 << dp.nwarp); ++w)
+            for (int l = 0; l < 32; ++l) {
+                const uint64_t g0 = gidx(layout_index(ln, rg, wp, dp.nreg, dp.nwarp, flip, l, 0, w));
+                for (int r = 0; r < (1 << dp.nreg); ++r) {
+                    uint64_t got = g0;
+                    for (int k = 0; k < dp.nreg; ++k)
+                        if ((r >> k) & 1) got ^= off[k];
+                    if (got != gidx(layout_index(ln, rg, wp, dp.nreg, dp.nwarp, flip, l, r, w))) return false;
+                }
+            }
+    }
+    return true;
 }
 
 static long g_groups = 0;  // merged phase groups seen
@@ -217,6 +254,14 @@ static void run_planned(const std::vector<DevOp>& ops, const DevPass& dp, std::v
                 for (int l = 0; l < 32; ++l)
                     for (int r = 0; r < P.R; ++r)
                         if ((r & 1) && !((r >> K) & 1)) std::swap(P.at(l, r, w), P.at(l, r ^ (1 | (1 << K)), w));
+        }
+        // DENSE, REAL, ANTI, IREAL and DIAG ops carry no conditions: the
+        // kernel tests none for them
+        const bool unconditioned = (h.code >= RC_DENSE_R && h.code <= RC_IREAL_L) ||
+                                   (h.code >= RC_DIAG_G && h.code <= RC_DIAG_R);
+        if (unconditioned && (o.cm_glob != 0 || h.cm_thr != 0 || h.cm_reg != 0)) {
+            std::printf("op with code %d carries conditions\n", int(h.code));
+            std::exit(1);
         }
         if ((base & o.cm_glob) != o.cm_glob) continue;
         const uint32_t cmr = h.cm_reg, cvr = h.cv_reg;
@@ -373,6 +418,12 @@ int main(int argc, char** argv) {
                 dp.nh = ps.nh;
                 std::vector<DevOp> planned = ops;
                 plan_register_layout(&dp, &planned, 16, reorder != 0);
+                for (int h = 0; h < ps.nh; ++h) dp.h[h] = ps.h[h];
+                set_register_offsets(&dp);
+                if (!check_register_offsets(dp)) {
+                    std::printf("register offsets disagree with the layout (circuit %d)\n", ci);
+                    return 1;
+                }
                 for (int trial = 0; trial < 2; ++trial) {
                     const uint64_t base = rng();
                     std::vector<cd> T(size_t(1) << tb);
