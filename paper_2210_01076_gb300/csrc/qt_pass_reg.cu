@@ -622,8 +622,14 @@ __device__ __forceinline__ void run_ops(typename A::cx (&x)[1 << RB], const DevO
             }
             const uint64_t cmg = op->cm_glob;
             if ((base & cmg) != cmg) continue;  // a control outside the tile is 0: uniform skip
-            const bool thr_ok = ((threadIdx.x ^ h.cv_thr) & h.cm_thr) == h.cm_thr;
-            const uint32_t cmr = h.cm_reg, cvr = h.cv_reg;
+            const uint32_t cmt = h.cm_thr, cmr = h.cm_reg, cvr = h.cv_reg;
+            if ((cmt | cmr) == 0) {
+                // no condition inside the tile (at most a control outside it)
+                if (code == RC_X_R) RO::x_reg0(x, true, 0u, 0u);
+                else RO::x_lane(x, h.a, true, 0u, 0u);
+                continue;
+            }
+            const bool thr_ok = ((threadIdx.x ^ h.cv_thr) & cmt) == cmt;
             if (code == RC_X_R) RO::x_reg0(x, thr_ok, cmr, cvr);
             else RO::x_lane(x, h.a, thr_ok, cmr, cvr);
             continue;
@@ -779,9 +785,12 @@ __global__ void __launch_bounds__(256, MG ? 2 : reg_min_blocks<A, RB>()) k_pass_
         tc::fence_after_sync();
         mc.tmem = s_tmem;
     }
-    const uint64_t base = tile_base(dp, worklist, blockIdx.x);
+    // the tile's first amplitude: one thread computes it for the CTA
+    __shared__ uint64_t s_base;
+    if (threadIdx.x == 0) s_base = tile_base(dp, worklist, blockIdx.x);
     chunk_offsets(dp, choff);
     __syncthreads();
+    const uint64_t base = s_base;
     const uint32_t lowmask = (1u << dp.lt) - 1u;
     // The amplitude index of tile index j is base | (j & lowmask) |
     // choff[j >> lt]: XOR-linear in j, with the base's bits disjoint from the
