@@ -763,6 +763,28 @@ def precision_block(B, W):
     return out
 
 
+def sharing_block(B, W, levels):
+    """What a copy-on-write checkpoint store (Section III-F) could share: the
+    mean fraction of partitions that a segment leaves unchanged
+    (qt_segment_touched, planned on the host with dry runs), at the
+    benchmarks' checkpoint spacings and at one level per checkpoint (the
+    paper's per-net state vectors)."""
+    def untouched(n, dtype, p, lv, G):
+        c = B.Circuit(n, dtype, p)
+        c.set_option("dry_run", 1)
+        c.set_option("ckpt_interval", G)
+        c.load_levels(lv)
+        c.update_state()
+        S = c.num_segments()
+        frac = float(np.mean([1.0 - c.segment_touched(s).mean() for s in range(S)]))
+        c.close()
+        return {"levels_per_checkpoint": G, "segments": S, "unchanged_partition_fraction": frac}
+    qft = W.qft_like_circuit(30, 2000, seed=7)
+    return {"incremental_n24": [untouched(N_QUBITS, "c128df", LOG2_PART, levels, G) for G in (1, CKPT)],
+            "qft_like_n30": [untouched(30, "c64", 18, qft, G) for G in (1, 8)],
+            "note": "partitions a segment leaves unchanged could be shared with the previous checkpoint"}
+
+
 def run_configs(args, levels):
     from paper_2210_01076_gb300 import binding as B
     from paper_2210_01076_gb300 import workloads as W
@@ -774,6 +796,7 @@ def run_configs(args, levels):
     out["deep_qft_n30"] = _guard(config3_block, B, W, peak, peak_kind)
     out["batch256"] = _guard(config4_block, B, W)
     out["precision_policy"] = _guard(precision_block, B, W)
+    out["checkpoint_sharing"] = _guard(sharing_block, B, W, levels)
     if args.configs_serve:
         sargs = argparse.Namespace(**vars(args))
         sargs.serve_seconds, sargs.serve_burst, sargs.serve_check = 1.0, 100, 0

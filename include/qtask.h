@@ -318,6 +318,16 @@ qt_status qt_num_segments(const qt_circuit* c, int32_t* out);
 qt_status qt_segment_info(const qt_circuit* c, int32_t seg, int32_t* first_level, int32_t* nlevels,
                           int32_t* npasses, uint8_t* dirty_out, uint8_t* worklist_out);
 
+/* Partitions that segment `seg` of the current plan can change: the union of
+ * its passes' supports (the partitions where every control and phase
+ * condition above the partition bits can hold; Section III-D).  On every
+ * other partition the state after the segment equals the state before it,
+ * so a copy-on-write checkpoint store (Section III-F) could share those
+ * partitions with the previous checkpoint.  touched_out: 2^(n -
+ * log2_partition) bytes, 1 = member.  Valid after a qt_update_state (real or
+ * dry run); QT_ERR_RANGE for a segment out of range. */
+qt_status qt_segment_touched(const qt_circuit* c, int32_t seg, uint8_t* touched_out);
+
 /* Message of the last failed call on c (or of the last failed qt_create,
  * qt_norm_static or batch call on this thread when c is NULL).  Valid until
  * the next call on c.  (No counterpart in the paper: its modifiers throw a

@@ -46,7 +46,7 @@ class qt_update_stats(ctypes.Structure):
 EXPORTED = ["qt_create", "qt_destroy", "qt_num_levels", "qt_num_gates", "qt_insert_level", "qt_remove_level",
             "qt_insert_gate", "qt_remove_gate", "qt_replace_gate", "qt_update_state", "qt_read_amplitudes",
             "qt_read_amplitudes_device", "qt_read_amplitudes_async", "qt_read_wait", "qt_norm", "qt_norm_static", "qt_fidelity", "qt_max_abs_diff", "qt_probabilities",
-            "qt_set_option", "qt_set_stream", "qt_num_segments", "qt_segment_info", "qt_last_error",
+            "qt_set_option", "qt_set_stream", "qt_num_segments", "qt_segment_info", "qt_segment_touched", "qt_last_error",
             "qt_batch_create", "qt_batch_run", "qt_batch_read_amplitudes", "qt_batch_destroy",
             "qt_batch_last_error",
             "qt_release_device", "qt_device_bytes", "qt_server_create", "qt_server_destroy",
@@ -148,6 +148,7 @@ def load(path: str = LIB_PATH):
         "qt_set_stream": [P, P],
         "qt_num_segments": [P, ctypes.POINTER(i32)],
         "qt_segment_info": [P, i32, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(i32), P, P],
+        "qt_segment_touched": [P, i32, P],
         "qt_release_device": [P],
         "qt_device_bytes": [P, ctypes.POINTER(i64)],
         "qt_server_create": [i32, i64, ctypes.POINTER(P)],
@@ -335,6 +336,12 @@ def qt_segment_info(h, seg: int, nparts: int):
             "worklist": Wk.astype(bool)}
 
 
+def qt_segment_touched(h, seg: int, nparts: int) -> np.ndarray:
+    T = np.zeros(nparts, np.uint8)
+    _check(h, load().qt_segment_touched(h, seg, T.ctypes.data))
+    return T.astype(bool)
+
+
 def qt_last_error(h) -> str:
     m = load().qt_last_error(h)
     return m.decode() if m else ""
@@ -449,6 +456,9 @@ class Circuit:
 
     def segment_info(self, seg: int):
         return qt_segment_info(self.h, seg, self.nparts)
+
+    def segment_touched(self, seg: int) -> np.ndarray:
+        return qt_segment_touched(self.h, seg, self.nparts)
 
     def load_levels(self, levels):
         """Append levels of gates; returns the gate ids level by level."""

@@ -1267,6 +1267,19 @@ qt_status qt_segment_info(const qt_circuit* cc, int32_t seg, int32_t* first_leve
     return QT_OK;
 }
 
+qt_status qt_segment_touched(const qt_circuit* cc, int32_t seg, uint8_t* touched_out) {
+    qt_circuit* c = const_cast<qt_circuit*>(cc);
+    if (!c || !touched_out) return QT_ERR_ARG;
+    if (!c->have_plan || seg < 0 || seg >= int32_t(c->supps.size()))
+        return fail(c, QT_ERR_RANGE, "segment out of range");
+    const uint32_t np = c->nparts();
+    Bitset U;
+    U.resize(np);
+    for (const Bitset& b : c->supps[seg]) U.or_with(b);
+    for (uint32_t q = 0; q < np; ++q) touched_out[q] = U.get(q) ? 1 : 0;
+    return QT_OK;
+}
+
 const char* qt_last_error(const qt_circuit* c) { return c ? c->err.c_str() : g_create_error.c_str(); }
 
 qt_status qt_release_device(qt_circuit* c) {

@@ -185,6 +185,44 @@ def test_tracker_covers_every_changed_partition(seed, G, p_multi, fusion):
         before = after
 
 
+def test_segment_touched_closed_forms():
+    """Section III-D: a gate changes only the partitions where its controls
+    (and a phase's own qubit) above the partition bits can be 1."""
+    n, p = 10, 6  # 16 partitions; qubits 6..9 are partition bits 0..3
+    c = dry(n, p, G=1)
+    c.load_levels([[W.make_gate("cz", [8, 0])], [W.make_gate("ccx", [1, 7, 9])], [W.make_gate("h", [0])],
+                   [W.make_gate("cp", [9, 6], [0.3])]])
+    c.update_state()
+    q = np.arange(16)
+    want = [(q >> 2) & 1 == 1, ((q >> 1) & 1 == 1) & ((q >> 3) & 1 == 1), np.ones(16, bool),
+            ((q >> 3) & 1 == 1) & (q & 1 == 1)]
+    assert c.num_segments() == 4
+    for s in range(4):
+        assert np.array_equal(c.segment_touched(s), want[s]), s
+    with pytest.raises(B.QtError):
+        c.segment_touched(4)
+
+
+@pytest.mark.parametrize("seed,G", [(1, 1), (2, 2), (3, 1)])
+def test_untouched_partitions_are_unchanged_by_the_segment(seed, G):
+    """What a copy-on-write checkpoint store would share (Section III-F): on
+    every partition outside qt_segment_touched the oracle's state after the
+    segment equals its state before, bit for bit."""
+    n, p = 9, 4
+    levels = W.random_circuit(n, 60, seed=seed, p_multi=0.7)
+    c = dry(n, p, G=G)
+    c.load_levels(levels)
+    c.update_state()
+    states = [oracle.simulate(n, [])] + boundary_states(n, levels, G)
+    shared = 0
+    for s in range(c.num_segments()):
+        t = c.segment_touched(s)
+        same = np.all(states[s + 1].reshape(1 << (n - p), 1 << p) == states[s].reshape(1 << (n - p), 1 << p), axis=1)
+        assert np.all(same[~t]), (s, np.flatnonzero(~t & ~same))
+        shared += int((~t).sum())
+    assert shared > 0
+
+
 def test_incremental_skips_segments_before_the_edit():
     n, p = 10, 5
     levels = W.random_circuit(n, 120, seed=9, p_multi=0.4)
