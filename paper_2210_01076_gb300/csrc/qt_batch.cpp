@@ -192,6 +192,7 @@ qt_status qt_batch_run(qt_batch* b, qt_batch_stats* stats) {
                 for (const HostOp& o : ps.ops) en.ops.push_back(encode_device_op(dtype, ps, o));
                 // batches run the kernel without merged phase groups
                 plan_register_layout(&dp, &en.ops, int(bytes_per_amp(dtype)), true, false);
+                if (dp.reg_kernel) set_register_offsets(&dp);
                 dp.nops = int32_t(en.ops.size());
                 if (!dp.reg_kernel || dp.nwarp != 3 || dp.nreg < 2 || dp.nreg > 4)
                     return bfail(b, QT_ERR_ARG,

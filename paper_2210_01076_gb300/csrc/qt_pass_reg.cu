@@ -542,10 +542,19 @@ __device__ __forceinline__ bool mma_block(typename A::cx (&x)[1 << RB], const De
     return true;
 }
 
+// Copy ops [c0, c0 + cn) of a pass into shared memory (all threads).
+__device__ __forceinline__ void stage_ops(DevOp* s_ops, const DevOp* __restrict__ pops, int c0, int cn) {
+    const uint4* srcv = reinterpret_cast<const uint4*>(pops + c0);
+    uint4* dstv = reinterpret_cast<uint4*>(s_ops);
+    constexpr int kVec = int(sizeof(DevOp) / sizeof(uint4));
+    for (int i = threadIdx.x; i < cn * kVec; i += blockDim.x) dstv[i] = srcv[i];
+}
+
+// s_ops: the caller's shared-memory staging area of kOpChunk ops.
 template <class A, int RB, bool PG, bool MG = false>
 __device__ __forceinline__ void run_ops(typename A::cx (&x)[1 << RB], const DevOp* __restrict__ pops, int nops,
                                         uint64_t base, uint32_t lane, uint32_t wid, typename A::amp_t* tile,
-                                        MmaCtx* mc = nullptr) {
+                                        DevOp* s_ops, MmaCtx* mc = nullptr) {
     using RO = RegOps<A, RB>;
     using cx = typename A::cx;
     constexpr int R = 1 << RB;
@@ -557,16 +566,13 @@ __device__ __forceinline__ void run_ops(typename A::cx (&x)[1 << RB], const DevO
     // of codes (measured faster than a jump table, and than loading the next
     // header early), and only the classes that can carry conditions (X,
     // SWAP, phases) test them.
-    __shared__ __align__(16) DevOp s_ops[kOpChunk];
     for (int c0 = 0; c0 < nops; c0 += kOpChunk) {
     const int cn = nops - c0 < kOpChunk ? nops - c0 : kOpChunk;
-    __syncthreads();  // the previous chunk has been read by all
-    {
-        const uint4* srcv = reinterpret_cast<const uint4*>(pops + c0);
-        uint4* dstv = reinterpret_cast<uint4*>(s_ops);
-        constexpr int kVec = int(sizeof(DevOp) / sizeof(uint4));
-        for (int i = threadIdx.x; i < cn * kVec; i += blockDim.x) dstv[i] = srcv[i];
-    }
+    // the previous chunk has been read by all.  (Before the first chunk no
+    // barrier is needed: every caller reaches run_ops after a barrier that
+    // follows all reads of its previous tile's ops, or with none.)
+    if (c0 > 0) __syncthreads();
+    stage_ops(s_ops, pops, c0, cn);
     __syncthreads();
     for (int oi = 0; oi < cn; ++oi) {
         const DevOp* op = s_ops + oi;
@@ -785,8 +791,11 @@ __global__ void __launch_bounds__(256, MG ? 2 : reg_min_blocks<A, RB>()) k_pass_
         tc::fence_after_sync();
         mc.tmem = s_tmem;
     }
-    // the tile's first amplitude: one thread computes it for the CTA
+    // the tile's first amplitude: one thread computes it for the CTA.  (The
+    // ops are staged after the tile's loads are issued, so that the two
+    // latencies overlap: staging them before this barrier measured slower.)
     __shared__ uint64_t s_base;
+    __shared__ __align__(16) DevOp s_ops[kOpChunk];
     if (threadIdx.x == 0) s_base = tile_base(dp, worklist, blockIdx.x);
     chunk_offsets(dp, choff);
     __syncthreads();
@@ -804,7 +813,7 @@ __global__ void __launch_bounds__(256, MG ? 2 : reg_min_blocks<A, RB>()) k_pass_
 #pragma unroll
         for (int r = 0; r < R; ++r) x[r] = A::ld(src[g ^ reg_offset<RB>(dp.rin, r)]);
     }
-    run_ops<A, RB, PG, MG>(x, ops + dp.op_offset, dp.nops, base, lane, wid, tile, &mc);
+    run_ops<A, RB, PG, MG>(x, ops + dp.op_offset, dp.nops, base, lane, wid, tile, s_ops, &mc);
     // A pass whose gates were all relabels has no ops, so no barrier has
     // separated the loads from the stores; its final layout sends amplitudes
     // to positions that other warps of the CTA load (in place: dst == src).
@@ -850,6 +859,7 @@ __global__ void __launch_bounds__(256, (RB <= 3 ? 3 : 1)) k_pass_tma(typename A:
     amp_t* tile = inbuf + (1u << tb);                   // layout changes
     __shared__ uint64_t choff[1 << kMaxTileHigh];
     __shared__ __align__(8) uint64_t bar;
+    __shared__ __align__(16) DevOp s_ops[kOpChunk];
     const uint32_t lane = threadIdx.x & 31u, wid = threadIdx.x >> 5;
     chunk_offsets(dp, choff);
     if (threadIdx.x == 0) {
@@ -888,7 +898,7 @@ __global__ void __launch_bounds__(256, (RB <= 3 ? 3 : 1)) k_pass_tma(typename A:
         }
         __syncthreads();  // inbuf is free: stage the next tile while computing this one
         if (t + gridDim.x < ntiles) issue(t + gridDim.x);
-        run_ops<A, RB, PG>(x, ops + dp.op_offset, dp.nops, base, lane, wid, tile);
+        run_ops<A, RB, PG>(x, ops + dp.op_offset, dp.nops, base, lane, wid, tile, s_ops);
         const TileMap<RB> m = layout_map<RB>(dp.fin, dp.nwarp, lane, wid);
 #pragma unroll
         for (int r = 0; r < R; ++r) {
@@ -1011,27 +1021,29 @@ __device__ __forceinline__ void batch_tile(typename A::amp_t* __restrict__ state
     using cx = typename A::cx;
     constexpr int R = 1 << RB;
     const uint32_t lane = threadIdx.x & 31u, wid = threadIdx.x >> 5;
-    const uint64_t base = tile_base(dp, nullptr, t);
+    __shared__ uint64_t s_base;  // the tile's first amplitude, computed by one thread
+    __shared__ __align__(16) DevOp s_ops[kOpChunk];
+    if (threadIdx.x == 0) s_base = tile_base(dp, nullptr, t);
     chunk_offsets(dp, choff);
     __syncthreads();
+    const uint64_t base = s_base;
     const uint32_t lowmask = (1u << dp.lt) - 1u;
     cx x[R];
     {
+        // amplitude indices as in k_pass_reg: the thread's index XOR the
+        // offsets of the register bits
         const TileMap<RB> m = initial_map<RB>(dp, lane, wid);
+        const uint64_t g = base | choff[m.thr >> dp.lt] | (m.thr & lowmask);
 #pragma unroll
-        for (int r = 0; r < R; ++r) {
-            const uint32_t j = m.idx(r);
-            x[r] = A::ld(__ldcg(&state[base | choff[j >> dp.lt] | (j & lowmask)]));  // L2: written by other SMs
-        }
+        for (int r = 0; r < R; ++r)
+            x[r] = A::ld(__ldcg(&state[g ^ reg_offset<RB>(dp.rin, r)]));  // L2: written by other SMs
     }
-    run_ops<A, RB, false>(x, ops + dp.op_offset, dp.nops, base, lane, wid, tile);
+    run_ops<A, RB, false>(x, ops + dp.op_offset, dp.nops, base, lane, wid, tile, s_ops);
     if (dp.nops == 0) __syncthreads();  // relabels only: the loads of every warp come before any store
     const TileMap<RB> m = layout_map<RB>(dp.fin, dp.nwarp, lane, wid);
+    const uint64_t g = base | choff[m.thr >> dp.lt] | (m.thr & lowmask);
 #pragma unroll
-    for (int r = 0; r < R; ++r) {
-        const uint32_t j = m.idx(r);
-        state[base | choff[j >> dp.lt] | (j & lowmask)] = A::st(x[r]);
-    }
+    for (int r = 0; r < R; ++r) state[g ^ reg_offset<RB>(dp.rout, r)] = A::st(x[r]);
     __threadfence();  // every thread's stores are visible device-wide before the tile is counted done
     __syncthreads();  // choff and tile are reused by the next item
 }
