@@ -303,7 +303,6 @@ def run_ours(args):
         ev1.record(stream)
         barrier()
         t_wall = time.perf_counter() - t_wall0
-    c.set_option("kernel_timing", 0)
     elapsed_ms = ev0.elapsed_time(ev1)
     clocks = clk.summary()
     amp = sum(s["amp_updates"] for s in stats)
@@ -317,12 +316,14 @@ def run_ours(args):
     t_max = t_max_s * 1e3
     value = amp_all / t_max_s
 
-    # ---- full re-simulation latency on the current circuit (same plan)
+    # ---- full re-simulation latency on the current circuit (same plan),
+    # timed like the rounds (with the per-launch events of kernel_timing)
     fulls, full_passes = [], 0
     for _ in range(3):
         fs = c.update_state(force_full=True)
         fulls.append(fs["gpu_ms"])
         full_passes = fs["passes_total"]
+    c.set_option("kernel_timing", 0)
     inc_lat = [s["gpu_ms"] for s in stats]
     # per-round incremental efficiency: the round's time over what a full
     # re-simulation of that round's circuit costs for the work left dirty
