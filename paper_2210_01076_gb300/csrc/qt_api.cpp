@@ -28,6 +28,7 @@
 #include <new>
 #include <stdexcept>
 #include <string>
+#include <unordered_map>
 #include <vector>
 
 #include "qt_internal.h"
@@ -107,11 +108,26 @@ struct qt_circuit {
     int plan_G = 0;
     std::vector<SegPlan> plans;
     std::vector<std::vector<Bitset>> supps;
+    std::vector<std::vector<qt_gate>> plan_gates;  // the gates each segment of the plan was planned from
     bool device_valid = false;
     bool state_stale = false;  // set by dry runs
 
     // introspection of the last update
     std::vector<Bitset> last_F, last_W;
+
+    // Encoded, layout-planned ops of the passes of the last update, by pass
+    // content: a pass the next update plans again (same ops, same tile) reuses
+    // them instead of being encoded and laid out anew.  Entries depend only on
+    // the pass and on enc_pp / enc_reg (cleared when those change); passes
+    // with tensor-core blocks are not kept.
+    struct EncPass {
+        Pass ps;
+        DevPass dp;  // the fields the layout planner and set_register_offsets fill
+        std::vector<DevOp> ops;
+    };
+    std::unordered_multimap<uint64_t, EncPass> enc_cache;
+    PlanParams enc_pp;
+    bool enc_reg = false;
 
     // device
     bool device_ready = false;
@@ -463,6 +479,59 @@ int effective_interval(const qt_circuit* c) {
     return int(std::min<int64_t>(G, 1 << 20));
 }
 
+// The gates of a segment compared field by field (angles bit for bit).
+bool same_gates(const std::vector<qt_gate>& a, const std::vector<qt_gate>& b) {
+    if (a.size() != b.size()) return false;
+    for (size_t i = 0; i < a.size(); ++i) {
+        const qt_gate &x = a[i], &y = b[i];
+        if (x.kind != y.kind || x.ntarget != y.ntarget || x.ncontrol != y.ncontrol) return false;
+        for (int k = 0; k < x.ntarget && k < 2; ++k)
+            if (x.target[k] != y.target[k]) return false;
+        for (int k = 0; k < x.ncontrol && k < 2; ++k)
+            if (x.control[k] != y.control[k]) return false;
+        if (std::memcmp(x.theta, y.theta, sizeof x.theta) != 0) return false;
+    }
+    return true;
+}
+
+// FNV-1a over what Pass::same_as compares (blocks aside: passes with blocks
+// are not cached).
+uint64_t pass_hash(const Pass& ps) {
+    uint64_t h = 1469598103934665603ull;
+    auto mix = [&h](const void* p, size_t n) {
+        const unsigned char* b = static_cast<const unsigned char*>(p);
+        for (size_t i = 0; i < n; ++i) {
+            h ^= b[i];
+            h *= 1099511628211ull;
+        }
+    };
+    mix(&ps.lt, sizeof ps.lt);
+    mix(&ps.nh, sizeof ps.nh);
+    mix(ps.h, sizeof(int32_t) * size_t(ps.nh));
+    for (const HostOp& o : ps.ops) {
+        mix(&o.kind, sizeof o.kind);
+        mix(&o.q0, sizeof o.q0);
+        mix(&o.q1, sizeof o.q1);
+        mix(&o.cmask, sizeof o.cmask);
+        mix(&o.ngates, sizeof o.ngates);
+        mix(o.m, sizeof o.m);
+    }
+    return h;
+}
+
+// The DevPass fields that plan_register_layout and set_register_offsets fill.
+void copy_planned_fields(const DevPass& from, DevPass* to) {
+    to->reg_kernel = from.reg_kernel;
+    to->nreg = from.nreg;
+    to->nwarp = from.nwarp;
+    std::memcpy(to->layout, from.layout, sizeof to->layout);
+    to->fin = from.fin;
+    to->groups = from.groups;
+    to->mma = from.mma;
+    std::memcpy(to->rin, from.rin, sizeof to->rin);
+    std::memcpy(to->rout, from.rout, sizeof to->rout);
+}
+
 qt_status do_update(qt_circuit* c, int force_full, qt_update_stats* stats) {
     auto t0 = std::chrono::steady_clock::now();
     qt_update_stats st;
@@ -479,16 +548,28 @@ qt_status do_update(qt_circuit* c, int force_full, qt_update_stats* stats) {
     std::vector<std::vector<Bitset>> nsupps(S);
     const uint32_t nparts = c->nparts();
     int64_t ngates_total = 0;
+    // a segment whose gates are those it was planned from last time (same
+    // parameters) keeps its plan: plan_segment is a function of both
+    std::vector<std::vector<qt_gate>> nseg_gates(S);
+    const bool reuse = c->have_plan && same_params(pp, c->plan_pp);
     for (int s = 0; s < S; ++s) {
         std::vector<const qt_gate*> gl;
         const int l0 = s * G, l1 = std::min(L, (s + 1) * G);
         for (int l = l0; l < l1; ++l)
             for (const Gate& g : c->levels[l].gates) gl.push_back(&g.g);
         ngates_total += int64_t(gl.size());
-        nplans[s] = plan_segment(gl, pp);
+        nseg_gates[s].reserve(gl.size());
+        for (const qt_gate* g : gl) nseg_gates[s].push_back(*g);
+        if (reuse && s < int(c->plans.size()) && s < int(c->plan_gates.size()) &&
+            same_gates(nseg_gates[s], c->plan_gates[s])) {
+            nplans[s] = c->plans[s];
+            nsupps[s] = c->supps[s];
+        } else {
+            nplans[s] = plan_segment(gl, pp);
+            for (const Pass& ps : nplans[s].passes) nsupps[s].push_back(pass_support(ps, nparts));
+        }
         nplans[s].first_level = l0;
         nplans[s].nlevels = l1 - l0;
-        for (const Pass& ps : nplans[s].passes) nsupps[s].push_back(pass_support(ps, nparts));
     }
     const bool params_changed = !c->have_plan || !same_params(pp, c->plan_pp) || G != c->plan_G;
     bool full = force_full || params_changed || (!c->dry_run && !c->device_valid);
@@ -504,6 +585,8 @@ qt_status do_update(qt_circuit* c, int force_full, qt_update_stats* stats) {
 
     // ---- track and schedule
     std::vector<Launch> launches;
+    if (!same_params(pp, c->enc_pp) || c->enc_reg != c->reg_kernel) c->enc_cache.clear();
+    std::unordered_multimap<uint64_t, qt_circuit::EncPass> next_cache;
     std::vector<DevOp> hops;
     std::vector<uint32_t> hwl;
     std::vector<float> hblk;  // operands B of the tensor-core blocks
@@ -621,12 +704,26 @@ qt_status do_update(qt_circuit* c, int force_full, qt_update_stats* stats) {
             dp.npart_log2 = c->n - c->p;
             dp.op_offset = int64_t(hops.size());
             std::vector<DevOp> pops;
-            pops.reserve(ps.ops.size());
-            for (const HostOp& o : ps.ops) pops.push_back(encode_op(c->dtype, ps, o, &hblk));
-            if (c->reg_kernel) {
-                plan_register_layout(&dp, &pops, int(bytes_per_amp(c->dtype)));
-                if (dp.reg_kernel) set_register_offsets(&dp);
+            const bool cacheable = ps.blocks.empty();
+            const uint64_t key = cacheable ? pass_hash(ps) : 0;
+            const qt_circuit::EncPass* hit = nullptr;
+            if (cacheable) {
+                auto range = c->enc_cache.equal_range(key);
+                for (auto it = range.first; it != range.second && !hit; ++it)
+                    if (it->second.ps.same_as(ps)) hit = &it->second;
             }
+            if (hit) {
+                pops = hit->ops;
+                copy_planned_fields(hit->dp, &dp);
+            } else {
+                pops.reserve(ps.ops.size());
+                for (const HostOp& o : ps.ops) pops.push_back(encode_op(c->dtype, ps, o, &hblk));
+                if (c->reg_kernel) {
+                    plan_register_layout(&dp, &pops, int(bytes_per_amp(c->dtype)));
+                    if (dp.reg_kernel) set_register_offsets(&dp);
+                }
+            }
+            if (cacheable) next_cache.emplace(key, qt_circuit::EncPass{ps, dp, pops});
             dp.tma = (dp.reg_kernel && c->tma) ? 1 : 0;
             dp.test_stall = c->test_stall ? 1 : 0;
             dp.nops = int32_t(pops.size());
@@ -634,6 +731,10 @@ qt_status do_update(qt_circuit* c, int force_full, qt_update_stats* stats) {
             launches.push_back(ln);
         }
     }
+
+    c->enc_cache.swap(next_cache);
+    c->enc_pp = pp;
+    c->enc_reg = c->reg_kernel;
 
     // ---- stats (plan side)
     st.segments_total = S;
@@ -747,6 +848,7 @@ qt_status do_update(qt_circuit* c, int force_full, qt_update_stats* stats) {
     // ---- commit
     c->plans = std::move(nplans);
     c->supps = std::move(nsupps);
+    c->plan_gates = std::move(nseg_gates);
     c->plan_pp = pp;
     c->plan_G = G;
     c->have_plan = true;
