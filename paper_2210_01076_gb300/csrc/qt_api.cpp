@@ -115,17 +115,18 @@ struct qt_circuit {
     // introspection of the last update
     std::vector<Bitset> last_F, last_W;
 
-    // Encoded, layout-planned ops of the passes of the last update, by pass
-    // content: a pass the next update plans again (same ops, same tile) reuses
-    // them instead of being encoded and laid out anew.  Entries depend only on
-    // the pass and on enc_pp / enc_reg (cleared when those change); passes
-    // with tensor-core blocks are not kept.
+    // Encoded, layout-planned ops of every pass of the last update's plan, by
+    // segment and pass: a pass the next update plans again (same ops, same
+    // tile) reuses them instead of being encoded and laid out anew.  Entries
+    // depend only on the pass and on enc_pp / enc_reg (cleared when those
+    // change); passes with tensor-core blocks are not kept.
     struct EncPass {
+        bool valid = false;
         Pass ps;
         DevPass dp;  // the fields the layout planner and set_register_offsets fill
         std::vector<DevOp> ops;
     };
-    std::unordered_multimap<uint64_t, EncPass> enc_cache;
+    std::vector<std::vector<EncPass>> enc;
     PlanParams enc_pp;
     bool enc_reg = false;
 
@@ -494,31 +495,6 @@ bool same_gates(const std::vector<qt_gate>& a, const std::vector<qt_gate>& b) {
     return true;
 }
 
-// FNV-1a over what Pass::same_as compares (blocks aside: passes with blocks
-// are not cached).
-uint64_t pass_hash(const Pass& ps) {
-    uint64_t h = 1469598103934665603ull;
-    auto mix = [&h](const void* p, size_t n) {
-        const unsigned char* b = static_cast<const unsigned char*>(p);
-        for (size_t i = 0; i < n; ++i) {
-            h ^= b[i];
-            h *= 1099511628211ull;
-        }
-    };
-    mix(&ps.lt, sizeof ps.lt);
-    mix(&ps.nh, sizeof ps.nh);
-    mix(ps.h, sizeof(int32_t) * size_t(ps.nh));
-    for (const HostOp& o : ps.ops) {
-        mix(&o.kind, sizeof o.kind);
-        mix(&o.q0, sizeof o.q0);
-        mix(&o.q1, sizeof o.q1);
-        mix(&o.cmask, sizeof o.cmask);
-        mix(&o.ngates, sizeof o.ngates);
-        mix(o.m, sizeof o.m);
-    }
-    return h;
-}
-
 // The DevPass fields that plan_register_layout and set_register_offsets fill.
 void copy_planned_fields(const DevPass& from, DevPass* to) {
     to->reg_kernel = from.reg_kernel;
@@ -585,8 +561,19 @@ qt_status do_update(qt_circuit* c, int force_full, qt_update_stats* stats) {
 
     // ---- track and schedule
     std::vector<Launch> launches;
-    if (!same_params(pp, c->enc_pp) || c->enc_reg != c->reg_kernel) c->enc_cache.clear();
-    std::unordered_multimap<uint64_t, qt_circuit::EncPass> next_cache;
+    if (!same_params(pp, c->enc_pp) || c->enc_reg != c->reg_kernel) c->enc.clear();
+    std::vector<std::vector<qt_circuit::EncPass>> next_enc(S);
+    // the cached encoding of pass i of segment s, if that pass is unchanged:
+    // at the same index, or at the same distance from the segment's end
+    auto cached = [&](int s, size_t i, const Pass& ps) -> qt_circuit::EncPass* {
+        if (!ps.blocks.empty() || s >= int(c->enc.size())) return nullptr;
+        std::vector<qt_circuit::EncPass>& old = c->enc[s];
+        const size_t nnew = nplans[s].passes.size();
+        for (size_t k : {i, i + old.size() - nnew}) {
+            if (k < old.size() && old[k].valid && old[k].ps.same_as(ps)) return &old[k];
+        }
+        return nullptr;
+    };
     std::vector<DevOp> hops;
     std::vector<uint32_t> hwl;
     std::vector<float> hblk;  // operands B of the tensor-core blocks
@@ -632,7 +619,17 @@ qt_status do_update(qt_circuit* c, int force_full, qt_update_stats* stats) {
         lastF[s] = F;
         lastW[s] = W;
         dirty_in = F;
-        if (!W.any()) continue;
+        next_enc[s].resize(np.passes.size());
+        if (!W.any()) {
+            // nothing to run: keep the segment's cached encodings for later updates
+            for (size_t i = 0; i < np.passes.size(); ++i) {
+                if (qt_circuit::EncPass* e = cached(s, i, np.passes[i])) {
+                    next_enc[s][i] = std::move(*e);
+                    e->valid = false;
+                }
+            }
+            continue;
+        }
         st.segments_run += 1;
         {
             // every gate of the segment is (re)applied to the recomputed partitions W
@@ -704,17 +701,12 @@ qt_status do_update(qt_circuit* c, int force_full, qt_update_stats* stats) {
             dp.npart_log2 = c->n - c->p;
             dp.op_offset = int64_t(hops.size());
             std::vector<DevOp> pops;
-            const bool cacheable = ps.blocks.empty();
-            const uint64_t key = cacheable ? pass_hash(ps) : 0;
-            const qt_circuit::EncPass* hit = nullptr;
-            if (cacheable) {
-                auto range = c->enc_cache.equal_range(key);
-                for (auto it = range.first; it != range.second && !hit; ++it)
-                    if (it->second.ps.same_as(ps)) hit = &it->second;
-            }
+            qt_circuit::EncPass* hit = cached(s, i, ps);
             if (hit) {
                 pops = hit->ops;
                 copy_planned_fields(hit->dp, &dp);
+                next_enc[s][i] = std::move(*hit);
+                hit->valid = false;
             } else {
                 pops.reserve(ps.ops.size());
                 for (const HostOp& o : ps.ops) pops.push_back(encode_op(c->dtype, ps, o, &hblk));
@@ -722,8 +714,8 @@ qt_status do_update(qt_circuit* c, int force_full, qt_update_stats* stats) {
                     plan_register_layout(&dp, &pops, int(bytes_per_amp(c->dtype)));
                     if (dp.reg_kernel) set_register_offsets(&dp);
                 }
+                if (ps.blocks.empty()) next_enc[s][i] = qt_circuit::EncPass{true, ps, dp, pops};
             }
-            if (cacheable) next_cache.emplace(key, qt_circuit::EncPass{ps, dp, pops});
             dp.tma = (dp.reg_kernel && c->tma) ? 1 : 0;
             dp.test_stall = c->test_stall ? 1 : 0;
             dp.nops = int32_t(pops.size());
@@ -732,7 +724,7 @@ qt_status do_update(qt_circuit* c, int force_full, qt_update_stats* stats) {
         }
     }
 
-    c->enc_cache.swap(next_cache);
+    c->enc.swap(next_enc);
     c->enc_pp = pp;
     c->enc_reg = c->reg_kernel;
 
