@@ -160,12 +160,14 @@ def test_server_at_served_sizes_against_the_oracle():
 
 
 def test_server_budget_evicts_and_stays_correct():
-    # a budget that holds the three largest circuits with their minimum of
-    # state, one checkpoint and one spare state each, but not all seven: the
-    # others are evicted and re-simulated in full when their turn comes
+    # a budget that admits the largest circuit with its state, one checkpoint
+    # and a spare state, but not the seven circuits' states and checkpoints
+    # together (they start resident): the first request already evicts, and
+    # evicted circuits are re-simulated in full when their turn comes
     def budget_for(_, circs):
         sizes = sorted((state_bytes(c) for c in circs), reverse=True)
-        return 3 * sum(sizes[:3])
+        assert 2 * sum(sizes) > 4 * sizes[0]
+        return 4 * sizes[0]
     ns, server_c, alone, mirrors, results, info = run_scenario(ncirc=7, nreq=30, workers=2, budget=budget_for,
                                                                seed=8)
     budget = budget_for(None, server_c)
