@@ -711,7 +711,7 @@ qt_status do_update(qt_circuit* c, int force_full, qt_update_stats* stats) {
                 pops.reserve(ps.ops.size());
                 for (const HostOp& o : ps.ops) pops.push_back(encode_op(c->dtype, ps, o, &hblk));
                 if (c->reg_kernel) {
-                    plan_register_layout(&dp, &pops, int(bytes_per_amp(c->dtype)));
+                    plan_register_layout(&dp, &pops, int(bytes_per_amp(c->dtype)), true, true, c->dtype == QT_C64);
                     if (dp.reg_kernel) set_register_offsets(&dp);
                 }
                 if (ps.blocks.empty()) next_enc[s][i] = qt_circuit::EncPass{true, ps, dp, pops};

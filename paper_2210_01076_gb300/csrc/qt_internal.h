@@ -179,7 +179,7 @@ static_assert(sizeof(TileLayout) == 20, "TileLayout layout");
 // kernel takes one branch per op.
 enum RegCode : uint8_t {
     RC_PERM = 0,
-    RC_DENSE_R, RC_DENSE_L,  // _R: target on register bit 0, _L: on lane bit a
+    RC_DENSE_R, RC_DENSE_L,  // _R: target on register bit 0 (DENSE: bit b), _L: on lane bit a
     RC_REAL_R, RC_REAL_L,
     RC_ANTI_R, RC_ANTI_L,
     RC_IREAL_R, RC_IREAL_L,
@@ -325,8 +325,12 @@ struct DevPass {
 // need a layout change.
 // phase_groups: merge runs of phases into RC_PH_GROUP ops where that is
 // estimated to save work (sets dp->groups).
+// dense_regk: a DENSE op whose target sits on register bit k > 0 keeps it
+// there (RegHdr::b = k; the kernel pairs registers across bit k) instead of
+// exchanging register bits 0 and k first (complex64, where the exchange's
+// moves are a large share of the op).
 void plan_register_layout(DevPass* dp, std::vector<DevOp>* ops, int coef_bytes, bool reorder = true,
-                          bool phase_groups = true);
+                          bool phase_groups = true, bool dense_regk = false);
 
 // Fill dp->rin / dp->rout from the planned layouts (needs lt and h).
 void set_register_offsets(DevPass* dp);

@@ -125,6 +125,20 @@ struct RegOps {
         }
     }
 
+    // a dense 2x2 on register bit K > 0: pairs (x[r], x[r | 2^K]) in place
+    template <int K>
+    static __device__ __forceinline__ void dense_regk(cx (&x)[R], const DevOp* op) {
+        const cx u00 = A::matp(op, 0), u01 = A::matp(op, 1), u10 = A::matp(op, 2), u11 = A::matp(op, 3);
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            if ((r >> K) & 1) continue;
+            const int r1 = r | (1 << K);
+            const cx a = x[r], b = x[r1];
+            x[r] = A::lin2(u00, a, u01, b);
+            x[r1] = A::lin2(u10, a, u11, b);
+        }
+    }
+
     static __device__ __forceinline__ void x_reg0(cx (&x)[R], bool thr_ok, uint32_t cmr, uint32_t cvr) {
 #pragma unroll
         for (int r = 0; r < R; r += 2) {
@@ -609,7 +623,21 @@ __device__ __forceinline__ void run_ops(typename A::cx (&x)[1 << RB], const DevO
                 // variants.
                 if (code & 1) {
                     if (code < RC_ANTI_R) {
-                        if (code == RC_DENSE_R) RO::template pair_reg0<OP_DENSE>(x, op);
+                        if (code == RC_DENSE_R) {
+                            // complex64 plans DENSE ops on register bit b in place
+                            if constexpr (std::is_same<A, ArF32>::value) {
+                                if (h.b > 0) {
+                                    dispatch_k<RB>(h.b, [&](auto kc) {
+                                        constexpr int K = decltype(kc)::value;
+                                        if constexpr (K > 0) RO::template dense_regk<K>(x, op);
+                                    });
+                                } else {
+                                    RO::template pair_reg0<OP_DENSE>(x, op);
+                                }
+                            } else {
+                                RO::template pair_reg0<OP_DENSE>(x, op);
+                            }
+                        }
                         else RO::template pair_reg0<OP_REAL>(x, op);
                     } else {
                         if (code == RC_ANTI_R) RO::template pair_reg0<OP_ANTI>(x, op);

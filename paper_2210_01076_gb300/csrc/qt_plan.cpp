@@ -772,7 +772,8 @@ void set_register_offsets(DevPass* dp) {
     }
 }
 
-void plan_register_layout(DevPass* dp, std::vector<DevOp>* ops_io, int coef_bytes, bool reorder, bool phase_groups) {
+void plan_register_layout(DevPass* dp, std::vector<DevOp>* ops_io, int coef_bytes, bool reorder, bool phase_groups,
+                          bool dense_regk) {
     const int tb = dp->lt + dp->nh;
     dp->reg_kernel = 0;
     dp->groups = 0;
@@ -1006,7 +1007,9 @@ void plan_register_layout(DevPass* dp, std::vector<DevOp>* ops_io, int coef_byte
             } else {
                 const int k = p - 8;
                 h.code = uint8_t(cr);
-                if (k > 0) {
+                if (k > 0 && dense_regk && o.kind == OP_DENSE) {
+                    h.b = int8_t(k);  // pairs across register bit k, layout unchanged
+                } else if (k > 0) {
                     // the kernel exchanges register bits 0 and k first
                     h.ren = int8_t(k);
                     auto x0k = [k](uint32_t v) -> uint32_t {

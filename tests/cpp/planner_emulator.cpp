@@ -16,7 +16,8 @@
 // blocks (their FP64 matrices, the ops moved ahead of them, the staging
 // masks and the layout after each block) the same way.  Each pass's register
 // offsets (the kernel's amplitude addressing) are checked against the layout
-// index of every position.  This pins the planner's bookkeeping on the
+// index of every position.  Half the circuits plan DENSE ops on register
+// bits in place (the complex64 option).  This pins the planner's bookkeeping on the
 // CPU; the GPU parity tests pin the kernels against the oracle.
 //
 // Build: g++ -O1 -std=c++17 -I<include> -I<csrc> -I<cuda include>
@@ -146,6 +147,7 @@ static bool check_register_offsets(const DevPass& dp) {
 
 static long g_groups = 0;  // merged phase groups seen
 static long g_blocks = 0;  // tensor-core blocks seen
+static long g_dense_k = 0;  // DENSE ops planned in place on a register bit above 0
 
 static void run_planned(const std::vector<DevOp>& ops, const DevPass& dp, std::vector<cd>& T, uint64_t base,
                         const std::vector<Block>* blocks = nullptr) {
@@ -264,6 +266,7 @@ static void run_planned(const std::vector<DevOp>& ops, const DevPass& dp, std::v
             std::exit(1);
         }
         if ((base & o.cm_glob) != o.cm_glob) continue;
+        if (h.code == RC_DENSE_R && h.b > 0) ++g_dense_k;
         const uint32_t cmr = h.cm_reg, cvr = h.cv_reg;
         auto rcond = [&](int r) { return ((uint32_t(r) ^ cvr) & cmr) == cmr; };
         Phys Q = P;  // values before the op (partners read from here)
@@ -273,10 +276,13 @@ static void run_planned(const std::vector<DevOp>& ops, const DevPass& dp, std::v
                 const bool thr_ok = ((ptid ^ h.cv_thr) & h.cm_thr) == h.cm_thr;
                 const int code = h.code;
                 if (code == RC_DENSE_R || code == RC_REAL_R || code == RC_IREAL_R) {
-                    for (int r = 0; r < P.R; r += 2) {
-                        const cd a = Q.at(l, r, w), b = Q.at(l, r + 1, w);
+                    const int K = code == RC_DENSE_R ? h.b : 0;  // DENSE may pair across register bit b
+                    for (int r = 0; r < P.R; ++r) {
+                        if ((r >> K) & 1) continue;
+                        const int r1 = r | (1 << K);
+                        const cd a = Q.at(l, r, w), b = Q.at(l, r1, w);
                         P.at(l, r, w) = entry(o, 0) * a + entry(o, 1) * b;
-                        P.at(l, r + 1, w) = entry(o, 2) * a + entry(o, 3) * b;
+                        P.at(l, r1, w) = entry(o, 2) * a + entry(o, 3) * b;
                     }
                 } else if (code == RC_DENSE_L || code == RC_REAL_L || code == RC_IREAL_L) {
                     const int hi = (l >> h.a) & 1, pl = l ^ (1 << h.a);
@@ -417,7 +423,7 @@ int main(int argc, char** argv) {
                 dp.lt = ps.lt;
                 dp.nh = ps.nh;
                 std::vector<DevOp> planned = ops;
-                plan_register_layout(&dp, &planned, 16, reorder != 0);
+                plan_register_layout(&dp, &planned, 16, reorder != 0, true, (ci & 1) != 0);
                 for (int h = 0; h < ps.nh; ++h) dp.h[h] = ps.h[h];
                 set_register_offsets(&dp);
                 if (!check_register_offsets(dp)) {
@@ -516,7 +522,7 @@ int main(int argc, char** argv) {
                 dp.lt = pf.lt;
                 dp.nh = pf.nh;
                 std::vector<DevOp> planned = ops;
-                plan_register_layout(&dp, &planned, 16, reorder != 0);
+                plan_register_layout(&dp, &planned, 16, reorder != 0, true, true);
                 if (!dp.mma || dp.nreg != 4 || dp.nwarp != 3) {
                     std::printf("a pass with blocks was not planned for the tensor-core kernel\n");
                     return 1;
@@ -537,6 +543,10 @@ int main(int argc, char** argv) {
             }
             ++nblk_passes;
         }
+    }
+    if (g_dense_k == 0) {
+        std::printf("no DENSE op was planned in place on a register bit\n");
+        return 1;
     }
     if (g_blocks == 0) {
         std::printf("no tensor-core block was planned\n");
