@@ -106,6 +106,7 @@ struct qt_circuit {
     bool have_plan = false;
     PlanParams plan_pp;
     int plan_G = 0;
+    bool plan_reg = true;  // reg_kernel when the plan was committed
     std::vector<SegPlan> plans;
     std::vector<std::vector<Bitset>> supps;
     std::vector<std::vector<qt_gate>> plan_gates;  // the gates each segment of the plan was planned from
@@ -547,7 +548,10 @@ qt_status do_update(qt_circuit* c, int force_full, qt_update_stats* stats) {
         nplans[s].first_level = l0;
         nplans[s].nlevels = l1 - l0;
     }
-    const bool params_changed = !c->have_plan || !same_params(pp, c->plan_pp) || G != c->plan_G;
+    // a change of kernel family (register or shared-memory kernel) re-runs
+    // everything, so the state always comes from the current options' kernels
+    const bool params_changed =
+        !c->have_plan || !same_params(pp, c->plan_pp) || G != c->plan_G || c->reg_kernel != c->plan_reg;
     bool full = force_full || params_changed || (!c->dry_run && !c->device_valid);
 
     // ---- device
@@ -843,6 +847,7 @@ qt_status do_update(qt_circuit* c, int force_full, qt_update_stats* stats) {
     c->plan_gates = std::move(nseg_gates);
     c->plan_pp = pp;
     c->plan_G = G;
+    c->plan_reg = c->reg_kernel;
     c->have_plan = true;
     c->last_F = std::move(lastF);
     c->last_W = std::move(lastW);

@@ -252,6 +252,38 @@ def test_incremental_bit_identical_unfused():
     run_edit_stream(11, 5, "c128df", 200, rounds=6, seed=4, G=2, fusion=0)
 
 
+@pytest.mark.parametrize("dtype", DTYPES)
+def test_option_changes_between_updates_match_a_fresh_circuit(dtype):
+    """The host keeps each segment's plan and each pass's encoded ops for the
+    next update; changing a planning option in between must plan anew: after
+    edits and an option change the state equals, bit for bit, a circuit built
+    fresh with the final gates and options, and the oracle."""
+    n, p = 13, 8
+    levels = W.random_circuit(n, 260, seed=31, p_multi=0.4)
+    model_levels = [list(lv) for lv in levels]
+    c, ids = build_circuit(n, levels, dtype, p, ckpt_interval=3)
+    c.update_state()
+    rng = np.random.default_rng(5)
+    opts = {"ckpt_interval": 3}
+    for key, val in (("tile_high", 3), ("merge", 0), ("fusion", 0), ("reg_kernel", 0), ("reg_kernel", 1),
+                     ("fusion", 1), ("tile_high", 5), ("merge", 1)):
+        lvl = int(rng.integers(len(model_levels) + 1))
+        g = W.random_gate(rng, n, 0.4)
+        c.insert_level(lvl)
+        c.insert_gate(lvl, g)
+        model_levels.insert(lvl, [g])
+        c.update_state()                      # an edit under the old options
+        c.set_option(key, val)
+        opts[key] = val
+        c.update_state()                      # the option change alone
+        fresh, _ = build_circuit(n, model_levels, dtype, p, **opts)
+        fresh.update_state()
+        assert np.array_equal(c.read_amplitudes().view(np.uint8), fresh.read_amplitudes().view(np.uint8)), (key, val)
+        fresh.close()
+    assert max_err(c.read_amplitudes(), oracle.simulate(n, W.flatten(model_levels))) <= TOL[dtype]
+    c.close()
+
+
 def test_remove_and_insert_levels_incremental():
     n, p = 10, 4
     levels = W.random_circuit(n, 150, seed=2, p_multi=0.4)
