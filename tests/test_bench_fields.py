@@ -2,7 +2,7 @@
 the lookup of ncu DRAM traffic (used only while the kernel sources still
 hash to the profiled ones), and the commands the ncu summaries under
 profiles/ give (each names committed files and flags that bench.py still
-accepts)."""
+accepts); also the host-only checkpoint-sharing block."""
 import json
 import os
 import re
@@ -74,3 +74,24 @@ def test_profile_commands_run_committed_files_with_current_flags():
                 assert flag in flags, (fn, flag)
             seen += 1
     assert seen >= 4
+
+
+def test_checkpoint_sharing_block_runs_on_the_host():
+    """configs.checkpoint_sharing plans dry runs only (no GPU): the shared
+    fraction of each spacing is a fraction, and small on these circuits
+    (every uncontrolled gate touches every partition)."""
+    from paper_2210_01076_gb300 import binding as B
+    from paper_2210_01076_gb300 import build as qbuild
+    from paper_2210_01076_gb300 import workloads as W
+    qbuild.build()
+    B.load()
+    levels, _, _, _ = bench.make_workload(bench.rank_seed(0), 2)
+    out = bench.sharing_block(B, W, levels)
+    for key in ("incremental_n24", "qft_like_n30"):
+        rows = out[key]
+        assert [r["levels_per_checkpoint"] for r in rows][0] == 1
+        for r in rows:
+            assert r["segments"] >= 1
+            assert 0.0 <= r["unchanged_partition_fraction"] <= 0.05
+        # one level per checkpoint shares at least as much as longer segments
+        assert rows[0]["unchanged_partition_fraction"] >= rows[-1]["unchanged_partition_fraction"]
